@@ -1,0 +1,297 @@
+"""Benchmark: GCUPS of the 3D Yee update, systolic vs naive schedule, FP32, 1 GB300.
+
+Workload (one bench "step" = one fdtd_step(2000) call of the whole hot path):
+256^3 grid, seeded Si/SiO2 permittivity map (eps 2.1 background with 8-20
+eps 12.1 slabs of 10x10 cross-section), PEC walls, sinusoidal point Jz dipole
+(wavelength 20 cells) at the centre, Courant number 0.99/sqrt(3), 2000 steps.
+GCUPS = cells * steps / seconds / 1e9.  The 470 MB of device state is larger
+than L2 (129 MB), so no L2 flush is needed between timed calls.
+
+Prints ONE JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(the reference arm), on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one per GPU (weak scaling; the
+path has no data exchange between GPUs in this build).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID = (256, 256, 256)
+STEPS_PER_CALL = 2000
+WAVELENGTH = 20.0
+# Algorithmic bytes per cell-step (fields FP32, coefficient FP32):
+STREAM_BYTES = 48.0                        # ideal one-pass stream: 6 read + 6 written
+NAIVE_BYTES = 76.0                         # two kernels: H 24R+12W, E 24R+4R+12W
+SHELL_CELLS, TILE_CELLS = 1217, 6975       # 32x16x16 ring, 31x15x15 updated
+SYSTOLIC_BYTES = SHELL_CELLS / TILE_CELLS * 52.0   # shell E,H read+write and eps read
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_workload(shape):
+    from paper_2502_20610_gb300 import workloads as wl
+    eps = wl.si_sio2_eps(shape, 1)
+    J = wl.sine_source(65536, wl.DT_DEFAULT, WAVELENGTH)
+    src = (2, shape[2] // 2, shape[1] // 2, shape[0] // 2)  # Jz at the centre cell
+    return eps, J, src
+
+
+def cpu_baseline(shape, budget_s=15.0):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded
+    sample of the workload: the same grid and geometry for as many steps as
+    fit in ~budget_s (at least 1)."""
+    from oracle import YeeOracle
+    from paper_2502_20610_gb300 import workloads as wl
+    eps, J, (c, i, j, k) = make_workload(shape)
+    o = YeeOracle(shape, wl.DT_DEFAULT, eps)
+    o.add_source(c, i, j, k, J)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(STEPS_PER_CALL, int(budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    cells = shape[0] * shape[1] * shape[2]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": cells * n / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{shape[2]}x{shape[1]}x{shape[0]} grid, same eps map and source, {n} steps "
+                      f"(of {STEPS_PER_CALL}), FP64, {dt:.1f} s"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return world, rank, local
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    cb = cpu_baseline(GRID, budget_s=float(os.environ.get("BENCH_CPU_BUDGET_S", "15")))
+    line = {"impl": "reference", "metric": "GCUPS of 3D Yee update (FP64 CPU oracle)",
+            "value": cb["value"], "unit": "GCUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config():
+    return {"workload": "256^3 Si/SiO2 eps map (seed 1), PEC walls, Jz dipole lambda=20 at the centre, "
+                        "2000 steps per call, FP32 fields",
+            "grid_xyz": list(GRID[::-1]), "steps_per_call": STEPS_PER_CALL,
+            "l2": "inputs larger than L2 (470 MB device state), no flush",
+            "parallelism": "replicas (one independent simulation per GPU)"}
+
+
+def time_calls(sim, n_calls, stream):
+    import torch
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(n_calls):
+        sim.step(STEPS_PER_CALL)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--naive-calls", type=int, default=1, help="timed naive calls (context)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    from paper_2502_20610_gb300 import fdtd
+    from paper_2502_20610_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(device)
+    shape = GRID
+    cells = shape[0] * shape[1] * shape[2]
+    eps, J, (c, i, j, k) = make_workload(shape)
+
+    sim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme="systolic", device=device,
+                   steps_per_launch=STEPS_PER_CALL, max_source_steps=J.size)
+    sim.add_source(c, i, j, k, J)
+    for _ in range(args.warmup):
+        sim.step(STEPS_PER_CALL)
+    sim.sync()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sim.launch_count
+    elapsed = time_calls(sim, args.steps, stream)
+    launches = sim.launch_count - l0
+    sim.sync()
+    clk = clocks.stop()
+    barrier(world)
+    elapsed = max_over_ranks(elapsed, world, device)
+    gcups = world * cells * STEPS_PER_CALL * args.steps / elapsed / 1e9
+
+    # naive schedule on the same workload (context for "systolic vs naive")
+    naive = None
+    if args.naive_calls > 0:
+        nsim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme="naive", device=device, max_source_steps=J.size)
+        nsim.add_source(c, i, j, k, J)
+        nsim.step(STEPS_PER_CALL)
+        nsim.sync()
+        t = time_calls(nsim, args.naive_calls, stream)
+        nsim.sync()
+        naive_gcups = cells * STEPS_PER_CALL * args.naive_calls / t / 1e9
+        naive = {"value": naive_gcups, "unit": "GCUPS", "ms_per_step": 1e3 * t / args.naive_calls,
+                 "kernels_per_step": 2 * STEPS_PER_CALL,
+                 "hbm_gbs_at_76B": naive_gcups * NAIVE_BYTES, "speedup_systolic": gcups / world / naive_gcups}
+        nsim.close()
+
+    # end to end through the public API with host buffers: H2D of the initial
+    # fields from pinned memory, the 2000 steps, D2H of the result
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(wl.random_fields(shape, 0)).pin_memory()
+        host_out = torch.empty((6,) + shape, dtype=torch.float32).pin_memory()
+        nb = 6 * cells * 4
+        sim.write_fields(host_in)
+        sim.step(STEPS_PER_CALL)
+        sim.read_fields(out=host_out)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sim.write_fields_ptr(host_in.data_ptr())
+            sim.step(STEPS_PER_CALL)
+            sim.read_fields_ptr(0x3F, host_out.data_ptr())
+        te = time.perf_counter() - t0
+        te = max_over_ranks(te, world, device)
+        e2e = {"value": world * cells * STEPS_PER_CALL * args.steps / te / 1e9, "unit": "GCUPS",
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+    sim.close()
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = load_peaks()
+    per_launch_s = elapsed / max(launches, 1)
+    cell_steps_per_launch = cells * STEPS_PER_CALL * args.steps / max(launches, 1)
+    achieved = SYSTOLIC_BYTES * cell_steps_per_launch / per_launch_s / 1e9
+    line = {
+        "metric": "GCUPS of 3D Yee update, systolic vs naive kernel, FP32 & FP16-stored, 1 GB300",
+        "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(),
+        "scheme": "systolic",
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "systolic_kernel",
+                     "algorithmic_bytes_per_cell_step": round(SYSTOLIC_BYTES, 3)},
+        "stream_roofline": {"bytes_per_cell_step": STREAM_BYTES,
+                            "bound_gcups": peak / STREAM_BYTES,
+                            "frac": gcups / world / (peak / STREAM_BYTES), "peak_kind": peak_kind},
+        "naive": naive,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(shape, budget_s=float(os.environ.get("BENCH_CPU_BUDGET_S", "15")))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

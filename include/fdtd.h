@@ -1,0 +1,176 @@
+/*
+ * fdtd.h — C ABI of libfdtd, a GB300 (sm_103a) Yee FDTD stepper with a
+ * systolic (skewed, temporally blocked) update scheme.
+ *
+ * Method: arxiv 2502.20610.  The update is the Yee leapfrog of Sec. 2, Eq. 1
+ * (Ex row printed; the Ey, Ez rows are its cyclic permutations and the H rows
+ * the forward-difference adjoint form), dx = dy = dz = 1, mu = 1:
+ *     H^{n+1/2} = H^{n-1/2} - dt * curl_f E^n
+ *     E^{n+1}   = E^n + (dt/eps) * curl_b H^{n+1/2}   (+ point sources)
+ * Two schedules compute it (both bit-identical in FP32):
+ *   FDTD_SCHEME_NAIVE    one kernel per half-step over the whole grid, the
+ *                        straightforward streaming update of Sec. 2;
+ *   FDTD_SCHEME_SYSTOLIC one persistent kernel per call in which each CTA
+ *                        keeps a subdomain on chip and scans it along the
+ *                        x-y-z-t diagonal, exchanging only boundary faces
+ *                        with neighbouring subdomains through global memory
+ *                        and per-subdomain progress flags, with no grid-wide
+ *                        synchronisation (Sec. 3, Fig. 7; Sec. 4).
+ *
+ * Conventions (every entry point):
+ *   * Grid nx*ny*nz cells; field arrays are nx*ny*nz values each, index
+ *     i + nx*(j + ny*k) (x fastest).  Cell (i,j,k) holds Ex(i+1/2,j,k),
+ *     Ey(i,j+1/2,k), Ez(i,j,k+1/2), Hx(i,j+1/2,k+1/2), Hy(i+1/2,j,k+1/2),
+ *     Hz(i+1/2,j+1/2,k).  Component order everywhere: Ex Ey Ez Hx Hy Hz.
+ *   * Boundary: PEC box [0,N]^3.  Tangential E on the three low planes is
+ *     never updated; E at index N reads as 0.
+ *   * State after n steps is (E^n, H^{n-1/2}); fdtd_step advances whole steps.
+ *   * Every call returns an fdtd_status and never aborts or exits.
+ *   * Pointers: "host" = host memory; "device" = CUDA device memory of the
+ *     current device; "any" = either (the CUDA runtime's unified addressing
+ *     tells them apart; pageable host memory is accepted, pinned is faster).
+ *   * Streams are passed as void* holding a cudaStream_t (NULL = legacy
+ *     default stream).  A handle is bound to one stream and is not
+ *     thread-safe; different handles are independent.
+ *   * Ownership: the caller allocates the device workspace (size from
+ *     fdtd_workspace_size) and keeps it alive until fdtd_destroy; the library
+ *     allocates nothing on the device.  Host-side state lives in the handle.
+ */
+#ifndef FDTD_H
+#define FDTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FDTD_OK = 0,
+    FDTD_ERR_INVALID_ARG = 1, /* a pointer, size or option is out of range */
+    FDTD_ERR_UNSUPPORTED = 2, /* a valid option this build does not implement */
+    FDTD_ERR_OOM = 3,         /* the workspace passed is smaller than required */
+    FDTD_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    FDTD_ERR_TIMEOUT = 5,     /* a device-side wait ran past wait_timeout_s */
+    FDTD_ERR_STATE = 6        /* call out of order, or state lost to an earlier error */
+} fdtd_status;
+
+enum { FDTD_SCHEME_NAIVE = 0, FDTD_SCHEME_SYSTOLIC = 1 };
+enum { FDTD_STORAGE_F32 = 0, FDTD_STORAGE_F16 = 1, FDTD_STORAGE_BF16 = 2 };
+enum { FDTD_BOUNDARY_PEC = 0, FDTD_BOUNDARY_GRADED_ABSORBER = 1, FDTD_BOUNDARY_LEARNED = 2 };
+
+typedef struct { int32_t nx, ny, nz; } fdtd_grid;
+
+typedef struct {
+    double dt;                /* time step; > 0; Courant limit dt < 1/sqrt(3) */
+    int32_t scheme;           /* FDTD_SCHEME_* */
+    int32_t storage;          /* FDTD_STORAGE_*; this build: F32 only */
+    float field_scale[6];     /* 16-bit storage scales (powers of two); unused for F32 */
+    int32_t tile[3];          /* systolic subdomain (updated cells per axis); 0 = default */
+    int32_t cluster[3];       /* systolic cluster shape; 0 = default (1,1,1) */
+    double wait_timeout_s;    /* bound on any device-side wait; <= 0 = 2 s */
+    int32_t max_source_steps; /* capacity of each source table; <= 0 = 65536 */
+    int32_t steps_per_launch; /* systolic: steps per persistent launch; <= 0 = 1024 */
+} fdtd_coeffs;
+
+typedef struct {
+    int32_t kind;       /* FDTD_BOUNDARY_*; this build: PEC only */
+    int32_t thickness;  /* absorber / learned layer thickness in cells */
+    double sigma_max;   /* graded absorber peak conductivity */
+    int32_t poly_order; /* graded absorber grading order */
+    const void *model;  /* learned boundary parameters (host) */
+} fdtd_boundary;
+
+typedef struct fdtd_sim *fdtd_handle;
+
+/* Bytes of device workspace a simulation with these parameters needs.
+ * Layout inside it is private.  Errors: INVALID_ARG (null pointer, grid
+ * dimension < 1, dt <= 0), UNSUPPORTED (storage or boundary not built). */
+fdtd_status fdtd_workspace_size(const fdtd_grid *grid, const fdtd_coeffs *coeffs,
+                                const fdtd_boundary *boundary, size_t *bytes);
+
+/* Create a simulation (Sec. 2 problem: fields on a PEC box, per-cell eps).
+ *   eps        host, nx*ny*nz doubles, relative permittivity > 0; copied.
+ *              The E coefficient dt/eps is formed in FP64 and rounded to
+ *              FP32 once per cell.
+ *   d_workspace device, >= fdtd_workspace_size bytes, 256-byte aligned,
+ *              caller-owned, must outlive the handle.
+ *   stream     cudaStream_t all work of the handle is ordered on.
+ * Fields start at zero and the step counter at 0.  Errors: INVALID_ARG,
+ * UNSUPPORTED, OOM (ws_bytes too small), CUDA. */
+fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coeffs *coeffs,
+                        const fdtd_boundary *boundary, void *d_workspace, size_t ws_bytes,
+                        void *stream, fdtd_handle *out);
+
+/* Add a point current source J on E component `component` (0..2 = Ex..Ez)
+ * of cell (i,j,k): after the E half-step of absolute step n,
+ *     E_c(i,j,k) += fl32(-(dt/eps_ijk) * J[n])     for 0 <= n < n_steps,
+ * nothing for later steps.  J is host, n_steps doubles (J at t_{n+1/2}),
+ * copied.  At most 16 sources; n_steps <= max_source_steps.  Not part of the
+ * paper's bare-bones benchmark (Sec. 4); used by the workloads.
+ * Errors: INVALID_ARG, UNSUPPORTED (H component), STATE (16 already), CUDA. */
+fdtd_status fdtd_add_source(fdtd_handle h, int32_t component, int32_t i, int32_t j, int32_t k,
+                            const double *J, int64_t n_steps);
+
+/* Overwrite all six fields with 6*nx*ny*nz floats (component-major, order
+ * Ex..Hz) from `src` (any).  Asynchronous on the handle's stream; `src` must
+ * stay valid until the stream reaches this point.  Clears an earlier device
+ * error.  Leaves the step counter unchanged.  Errors: INVALID_ARG, CUDA. */
+fdtd_status fdtd_write_fields(fdtd_handle h, const float *src);
+
+/* Advance n >= 0 whole steps with the handle's scheme.  Asynchronous:
+ * returns once the kernels are enqueued; launch errors are returned here,
+ * device-side wait timeouts at the next fdtd_sync / fdtd_read_fields.
+ * Errors: INVALID_ARG (n < 0), STATE (an earlier device error not cleared
+ * by fdtd_write_fields), CUDA. */
+fdtd_status fdtd_step(fdtd_handle h, int64_t n);
+
+/* Copy the components selected by `component_mask` (bit c = component c) as
+ * FP32, packed in component order, nx*ny*nz floats each, into `dst` (any).
+ * Synchronises the stream and checks the device error word first.
+ * Errors: INVALID_ARG, TIMEOUT (a device wait ran out; no data copied), CUDA. */
+fdtd_status fdtd_read_fields(fdtd_handle h, uint32_t component_mask, float *dst);
+
+/* Synchronise the handle's stream and report any device-side error.
+ * Errors: TIMEOUT, CUDA. */
+fdtd_status fdtd_sync(fdtd_handle h);
+
+/* Absolute step counter (number of steps taken since create, or the value
+ * set last by fdtd_set_current_step); -1 for a null handle. */
+int64_t fdtd_current_step(fdtd_handle h);
+
+/* Set the absolute step counter (indexes the source tables), e.g. after
+ * restoring a checkpoint with fdtd_write_fields.  Errors: INVALID_ARG. */
+fdtd_status fdtd_set_current_step(fdtd_handle h, int64_t step);
+
+/* Number of kernels this handle has launched so far. */
+int64_t fdtd_launch_count(fdtd_handle h);
+
+/* Static description of a status code; never NULL. */
+const char *fdtd_status_string(fdtd_status s);
+
+/* Release the handle's host state (the workspace stays the caller's).
+ * Does not synchronise; NULL is ignored. */
+void fdtd_destroy(fdtd_handle h);
+
+/* Test hooks for the systolic scheduler (no effect on the naive scheme):
+ *   FDTD_DEBUG_NONE          clear hooks;
+ *   FDTD_DEBUG_SKIP_PUBLISH  the subdomain with ticket `ticket` never
+ *                            publishes its progress, so its neighbours' waits
+ *                            run out: the launch ends with FDTD_ERR_TIMEOUT
+ *                            (failure-detection test; no GPU fault);
+ *   FDTD_DEBUG_DELAY         subdomains whose ticket % param == ticket sleep
+ *                            ~param2 ns before publishing each step;
+ *   FDTD_DEBUG_ORDER         hand out subdomains in another valid
+ *                            topological order (param: 1 = random tie-break
+ *                            seeded by ticket, 2 = lexicographic k,j,i).
+ * Errors: INVALID_ARG. */
+enum { FDTD_DEBUG_NONE = 0, FDTD_DEBUG_SKIP_PUBLISH = 1, FDTD_DEBUG_DELAY = 2, FDTD_DEBUG_ORDER = 3 };
+fdtd_status fdtd_debug_set(fdtd_handle h, int32_t kind, int64_t ticket, int64_t param, int64_t param2);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_H */

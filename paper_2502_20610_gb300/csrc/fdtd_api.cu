@@ -1,0 +1,457 @@
+// Host side of libfdtd: argument checks, workspace layout, coefficients,
+// source tables, the systolic tile schedule, and kernel launches.
+// The C ABI is declared (and documented) in include/fdtd.h.
+#include "fdtd.h"
+#include "internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+constexpr int DEFAULT_SOURCE_STEPS = 65536;
+constexpr int DEFAULT_STEPS_PER_LAUNCH = 1024;
+constexpr unsigned EPOCH_LIMIT = 1u << 30;
+
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    size_t fields[6], ce, src, progress, tiles, ctrl, total;
+    int gx, gy, gz;
+    long long ntiles_max;
+    int source_steps, steps_per_launch;
+};
+
+int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Everything lives in the caller's workspace:
+//   6 FP32 field arrays, the FP32 coefficient dt/eps, the source tables,
+//   and (systolic) one progress flag per skewed tile plus the tile order.
+bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, Layout &L)
+{
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    size_t off = 0;
+    for (int k = 0; k < 6; ++k) {
+        L.fields[k] = off;
+        off = align_up(off + sizeof(float) * (size_t)n);
+    }
+    L.ce = off;
+    off = align_up(off + sizeof(float) * (size_t)n);
+    L.source_steps = c.max_source_steps > 0 ? c.max_source_steps : DEFAULT_SOURCE_STEPS;
+    L.src = off;
+    off = align_up(off + sizeof(float) * (size_t)FDTD_MAX_SOURCES * (size_t)L.source_steps);
+    L.steps_per_launch = c.steps_per_launch > 0 ? c.steps_per_launch : DEFAULT_STEPS_PER_LAUNCH;
+    L.gx = L.gy = L.gz = 0;
+    L.ntiles_max = 0;
+    if (c.scheme == FDTD_SCHEME_SYSTOLIC) {
+        const long long T = L.steps_per_launch;
+        L.gx = ceil_div(g.nx + T - 1, SYS_NX);
+        L.gy = ceil_div(g.ny + T - 1, SYS_NY);
+        L.gz = ceil_div(g.nz + T - 1, SYS_NZ);
+        L.ntiles_max = (long long)L.gx * L.gy * L.gz;
+        if (L.ntiles_max > (1ll << 31) - 1) return false;
+    }
+    L.progress = off;
+    off = align_up(off + sizeof(unsigned) * (size_t)L.ntiles_max);
+    L.tiles = off;
+    off = align_up(off + sizeof(int) * (size_t)L.ntiles_max);
+    L.ctrl = off;
+    off = align_up(off + 64 * sizeof(int));
+    L.total = off;
+    return true;
+}
+
+fdtd_status check_args(const fdtd_grid *g, const fdtd_coeffs *c, const fdtd_boundary *b)
+{
+    if (!g || !c || !b) return FDTD_ERR_INVALID_ARG;
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return FDTD_ERR_INVALID_ARG;
+    if (g->nx > (1 << 20) || g->ny > (1 << 20) || g->nz > (1 << 20)) return FDTD_ERR_INVALID_ARG;
+    if (!(c->dt > 0.0) || !std::isfinite(c->dt)) return FDTD_ERR_INVALID_ARG;
+    if (c->scheme != FDTD_SCHEME_NAIVE && c->scheme != FDTD_SCHEME_SYSTOLIC) return FDTD_ERR_INVALID_ARG;
+    if (c->storage < FDTD_STORAGE_F32 || c->storage > FDTD_STORAGE_BF16) return FDTD_ERR_INVALID_ARG;
+    if (c->storage != FDTD_STORAGE_F32) return FDTD_ERR_UNSUPPORTED;
+    for (int a = 0; a < 3; ++a) {
+        if (c->tile[a] < 0 || c->cluster[a] < 0) return FDTD_ERR_INVALID_ARG;
+    }
+    const int tdef[3] = {SYS_NX, SYS_NY, SYS_NZ};
+    for (int a = 0; a < 3; ++a) {
+        if (c->tile[a] != 0 && c->tile[a] != tdef[a]) return FDTD_ERR_UNSUPPORTED;
+        if (c->cluster[a] > 1) return FDTD_ERR_UNSUPPORTED;
+    }
+    if (b->kind < FDTD_BOUNDARY_PEC || b->kind > FDTD_BOUNDARY_LEARNED) return FDTD_ERR_INVALID_ARG;
+    if (b->kind != FDTD_BOUNDARY_PEC) return FDTD_ERR_UNSUPPORTED;
+    return FDTD_OK;
+}
+
+// Skewed-tile schedule.  Tile (I,J,K) covers sigma in [A, A+n) with
+// A = (I*31, J*15, K*15) and is active at steps [start, end] of a launch of
+// T steps (its footprint A-t .. A-t+n intersects the domain).  Tiles with
+// start <= end+1 are kept (those with start = end+1 only relay progress),
+// ordered by (start, I+J+K): a topological order of the face-neighbour
+// dependencies in which subdomains that can run early are handed out first.
+struct TileEntry {
+    int start, diag;
+    unsigned key;
+    int id;
+};
+
+void build_tiles(const fdtd_grid &g, const Layout &L, int order, unsigned seed,
+                 std::vector<int> &tiles, std::vector<long long> &count_le)
+{
+    const int T = L.steps_per_launch;
+    std::vector<TileEntry> v;
+    v.reserve((size_t)std::min<long long>(L.ntiles_max, 1ll << 26));
+    for (int K = 0; K < L.gz; ++K)
+        for (int J = 0; J < L.gy; ++J)
+            for (int I = 0; I < L.gx; ++I) {
+                const int ax = I * SYS_NX, ay = J * SYS_NY, az = K * SYS_NZ;
+                const int s = std::max(0, std::max(ax - g.nx + 1, std::max(ay - g.ny + 1, az - g.nz + 1)));
+                const int ge = std::min(ax + SYS_NX - 1, std::min(ay + SYS_NY - 1, az + SYS_NZ - 1));
+                const int e = std::min(T - 1, ge);
+                if (s > e + 1) continue;
+                TileEntry te;
+                te.start = s;
+                te.id = I + L.gx * (J + L.gy * K);
+                if (order == 2) {
+                    te.diag = K;
+                    te.key = (unsigned)(J * L.gx + I);
+                } else {
+                    te.diag = I + J + K;
+                    unsigned h = (unsigned)te.id * 2654435761u ^ seed;
+                    h ^= h >> 15;
+                    h *= 2246822519u;
+                    h ^= h >> 13;
+                    te.key = order == 1 ? h : (unsigned)te.id;
+                }
+                v.push_back(te);
+            }
+    std::sort(v.begin(), v.end(), [](const TileEntry &a, const TileEntry &b) {
+        if (a.start != b.start) return a.start < b.start;
+        if (a.diag != b.diag) return a.diag < b.diag;
+        return a.key < b.key;
+    });
+    tiles.resize(v.size());
+    count_le.assign((size_t)T + 2, 0);
+    for (size_t q = 0; q < v.size(); ++q) {
+        tiles[q] = v[q].id;
+        count_le[(size_t)std::min(v[q].start, T + 1)]++;
+    }
+    for (size_t s = 1; s < count_le.size(); ++s) count_le[s] += count_le[s - 1];
+}
+
+} // namespace
+
+struct fdtd_sim {
+    fdtd_grid g;
+    fdtd_coeffs c;
+    fdtd_boundary b;
+    cudaStream_t stream;
+    char *ws;
+    Layout L;
+    float *f[6];
+    float *ce;
+    float *src_tab;
+    unsigned *progress;
+    int *tiles;
+    int *ctrl;
+    SrcSet src;
+    std::vector<double> eps_host;
+    long long step;
+    unsigned epoch;
+    long long launches;
+    int max_ctas;
+    std::vector<long long> count_le;  // tiles with start <= s
+    int dbg_kind;
+    long long dbg_ticket, dbg_param, dbg_param2;
+    bool failed;
+};
+
+namespace {
+
+fdtd_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return FDTD_OK;
+    std::fprintf(stderr, "libfdtd: CUDA error: %s\n", cudaGetErrorString(e));
+    return FDTD_ERR_CUDA;
+}
+
+#define CK(x)                                                                  \
+    do {                                                                       \
+        cudaError_t e_ = (x);                                                  \
+        if (e_ != cudaSuccess) return cuda_status(e_);                         \
+    } while (0)
+
+fdtd_status upload_tiles(fdtd_sim *h, int order, unsigned seed)
+{
+    std::vector<int> tiles;
+    build_tiles(h->g, h->L, order, seed, tiles, h->count_le);
+    if (!tiles.empty())
+        CK(cudaMemcpyAsync(h->tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice,
+                           h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+fdtd_status fdtd_workspace_size(const fdtd_grid *grid, const fdtd_coeffs *coeffs,
+                                const fdtd_boundary *boundary, size_t *bytes)
+{
+    if (!bytes) return FDTD_ERR_INVALID_ARG;
+    fdtd_status s = check_args(grid, coeffs, boundary);
+    if (s != FDTD_OK) return s;
+    Layout L;
+    if (!make_layout(*grid, *coeffs, L)) return FDTD_ERR_UNSUPPORTED;
+    *bytes = L.total;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coeffs *coeffs,
+                        const fdtd_boundary *boundary, void *d_workspace, size_t ws_bytes,
+                        void *stream, fdtd_handle *out)
+{
+    if (!out) return FDTD_ERR_INVALID_ARG;
+    *out = nullptr;
+    fdtd_status s = check_args(grid, coeffs, boundary);
+    if (s != FDTD_OK) return s;
+    if (!eps || !d_workspace || ((uintptr_t)d_workspace % ALIGN) != 0) return FDTD_ERR_INVALID_ARG;
+    Layout L;
+    if (!make_layout(*grid, *coeffs, L)) return FDTD_ERR_UNSUPPORTED;
+    if (ws_bytes < L.total) return FDTD_ERR_OOM;
+    const long long n = (long long)grid->nx * grid->ny * grid->nz;
+    for (long long p = 0; p < n; ++p)
+        if (!(eps[p] > 0.0) || !std::isfinite(eps[p])) return FDTD_ERR_INVALID_ARG;
+
+    fdtd_sim *h = new (std::nothrow) fdtd_sim();
+    if (!h) return FDTD_ERR_INVALID_ARG;
+    h->g = *grid;
+    h->c = *coeffs;
+    h->b = *boundary;
+    h->stream = (cudaStream_t)stream;
+    h->ws = (char *)d_workspace;
+    h->L = L;
+    for (int k = 0; k < 6; ++k) h->f[k] = (float *)(h->ws + L.fields[k]);
+    h->ce = (float *)(h->ws + L.ce);
+    h->src_tab = (float *)(h->ws + L.src);
+    h->progress = (unsigned *)(h->ws + L.progress);
+    h->tiles = (int *)(h->ws + L.tiles);
+    h->ctrl = (int *)(h->ws + L.ctrl);
+    h->src.n = 0;
+    h->step = 0;
+    h->epoch = 1;
+    h->launches = 0;
+    h->dbg_kind = FDTD_DEBUG_NONE;
+    h->dbg_ticket = h->dbg_param = h->dbg_param2 = 0;
+    h->failed = false;
+    h->eps_host.assign(eps, eps + n);
+
+    auto fail = [&](fdtd_status st) {
+        delete h;
+        return st;
+    };
+    // E coefficient: dt/eps in FP64, rounded to FP32 once per cell
+    std::vector<float> ce((size_t)n);
+    for (long long p = 0; p < n; ++p) ce[(size_t)p] = (float)(coeffs->dt / eps[p]);
+    cudaError_t e = cudaMemcpyAsync(h->ce, ce.data(), sizeof(float) * (size_t)n, cudaMemcpyHostToDevice,
+                                    h->stream);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        e = cudaMemsetAsync(h->f[k], 0, sizeof(float) * (size_t)n, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ctrl, 0, 64 * sizeof(int), h->stream);
+    if (e == cudaSuccess && L.ntiles_max > 0)
+        e = cudaMemsetAsync(h->progress, 0, sizeof(unsigned) * (size_t)L.ntiles_max, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+
+    if (coeffs->scheme == FDTD_SCHEME_SYSTOLIC) {
+        e = systolic_configure();
+        if (e != cudaSuccess) return fail(cuda_status(e));
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+        const int per_sm = systolic_max_ctas_per_sm();
+        if (per_sm < 1) return fail(FDTD_ERR_UNSUPPORTED);
+        h->max_ctas = sms * per_sm;
+        fdtd_status st = upload_tiles(h, 0, 0);
+        if (st != FDTD_OK) return fail(st);
+    }
+    *out = h;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_add_source(fdtd_handle h, int32_t component, int32_t i, int32_t j, int32_t k,
+                            const double *J, int64_t n_steps)
+{
+    if (!h || (!J && n_steps > 0) || n_steps < 0) return FDTD_ERR_INVALID_ARG;
+    if (component < 0 || component > 5) return FDTD_ERR_INVALID_ARG;
+    if (component > 2) return FDTD_ERR_UNSUPPORTED;
+    if (i < 0 || j < 0 || k < 0 || i >= h->g.nx || j >= h->g.ny || k >= h->g.nz) return FDTD_ERR_INVALID_ARG;
+    if (n_steps > h->L.source_steps) return FDTD_ERR_INVALID_ARG;
+    if (h->src.n >= FDTD_MAX_SOURCES) return FDTD_ERR_STATE;
+    const long long idx = i + (long long)h->g.nx * (j + (long long)h->g.ny * k);
+    const double c = h->c.dt / h->eps_host[(size_t)idx];
+    std::vector<float> amp((size_t)std::max<int64_t>(n_steps, 1));
+    for (int64_t n = 0; n < n_steps; ++n) amp[(size_t)n] = (float)(-c * J[n]);
+    float *dst = h->src_tab + (size_t)h->src.n * (size_t)h->L.source_steps;
+    if (n_steps > 0) {
+        CK(cudaMemcpyAsync(dst, amp.data(), sizeof(float) * (size_t)n_steps, cudaMemcpyHostToDevice,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    SrcDesc &s = h->src.s[h->src.n++];
+    s.comp = component;
+    s.i = i;
+    s.j = j;
+    s.k = k;
+    s.idx = idx;
+    s.n_amp = n_steps;
+    s.amp = dst;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_write_fields(fdtd_handle h, const float *src)
+{
+    if (!h || !src) return FDTD_ERR_INVALID_ARG;
+    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    for (int k = 0; k < 6; ++k)
+        CK(cudaMemcpyAsync(h->f[k], src + (size_t)k * n, sizeof(float) * n, cudaMemcpyDefault, h->stream));
+    CK(cudaMemsetAsync(h->ctrl + 1, 0, 3 * sizeof(int), h->stream));
+    h->failed = false;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_step(fdtd_handle h, int64_t n)
+{
+    if (!h || n < 0) return FDTD_ERR_INVALID_ARG;
+    if (h->failed) return FDTD_ERR_STATE;
+    if (h->c.scheme == FDTD_SCHEME_NAIVE) {
+        const float ndt = -(float)h->c.dt;
+        for (int64_t s = 0; s < n; ++s) {
+            CK(launch_naive_h(h->f, h->g.nx, h->g.ny, h->g.nz, ndt, h->stream));
+            CK(launch_naive_e(h->f, h->ce, h->g.nx, h->g.ny, h->g.nz, h->step, h->src, h->stream));
+            h->launches += 2;
+            h->step += 1;
+        }
+        return FDTD_OK;
+    }
+    while (n > 0) {
+        const int T = (int)std::min<int64_t>(n, h->L.steps_per_launch);
+        if (h->epoch + (unsigned)T + 1u > EPOCH_LIMIT) {
+            CK(cudaMemsetAsync(h->progress, 0, sizeof(unsigned) * (size_t)h->L.ntiles_max, h->stream));
+            h->epoch = 1;
+        }
+        CK(cudaMemsetAsync(h->ctrl, 0, sizeof(int), h->stream));  // ticket counter
+        SysLaunch p;
+        for (int k = 0; k < 6; ++k) p.f[k] = h->f[k];
+        p.ce = h->ce;
+        p.nx = h->g.nx;
+        p.ny = h->g.ny;
+        p.nz = h->g.nz;
+        p.gx = h->L.gx;
+        p.gy = h->L.gy;
+        p.gz = h->L.gz;
+        p.T = T;
+        p.epoch = h->epoch;
+        p.step0 = h->step;
+        p.tiles = h->tiles;
+        p.ntiles = (int)h->count_le[(size_t)T];
+        p.progress = h->progress;
+        p.ctrl = h->ctrl;
+        p.neg_dt = -(float)h->c.dt;
+        const double to = h->c.wait_timeout_s > 0 ? h->c.wait_timeout_s : 2.0;
+        p.timeout_ns = (long long)(to * 1e9);
+        p.dbg_kind = h->dbg_kind;
+        p.dbg_ticket = h->dbg_ticket;
+        p.dbg_param = h->dbg_param;
+        p.dbg_param2 = h->dbg_param2;
+        p.src = h->src;
+        const int grid = (int)std::max<long long>(1, std::min<long long>(p.ntiles, h->max_ctas));
+        CK(launch_systolic(p, grid, h->stream));
+        h->launches += 1;
+        h->epoch += (unsigned)T + 1u;
+        h->step += T;
+        n -= T;
+    }
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_sync(fdtd_handle h)
+{
+    if (!h) return FDTD_ERR_INVALID_ARG;
+    int host_ctrl[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(host_ctrl, h->ctrl, sizeof(host_ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (host_ctrl[1] != DEV_OK) {
+        h->failed = true;
+        return FDTD_ERR_TIMEOUT;
+    }
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_read_fields(fdtd_handle h, uint32_t component_mask, float *dst)
+{
+    if (!h || (!dst && component_mask) || component_mask > 63u) return FDTD_ERR_INVALID_ARG;
+    fdtd_status s = fdtd_sync(h);
+    if (s != FDTD_OK) return s;
+    const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    size_t q = 0;
+    for (int k = 0; k < 6; ++k) {
+        if (!(component_mask & (1u << k))) continue;
+        CK(cudaMemcpyAsync(dst + q * n, h->f[k], sizeof(float) * n, cudaMemcpyDefault, h->stream));
+        ++q;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
+int64_t fdtd_current_step(fdtd_handle h) { return h ? h->step : -1; }
+
+fdtd_status fdtd_set_current_step(fdtd_handle h, int64_t step)
+{
+    if (!h || step < 0) return FDTD_ERR_INVALID_ARG;
+    h->step = step;
+    return FDTD_OK;
+}
+
+int64_t fdtd_launch_count(fdtd_handle h) { return h ? h->launches : -1; }
+
+const char *fdtd_status_string(fdtd_status s)
+{
+    switch (s) {
+    case FDTD_OK: return "ok";
+    case FDTD_ERR_INVALID_ARG: return "invalid argument";
+    case FDTD_ERR_UNSUPPORTED: return "unsupported option";
+    case FDTD_ERR_OOM: return "workspace too small";
+    case FDTD_ERR_CUDA: return "CUDA error";
+    case FDTD_ERR_TIMEOUT: return "device wait timed out";
+    case FDTD_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+void fdtd_destroy(fdtd_handle h) { delete h; }
+
+fdtd_status fdtd_debug_set(fdtd_handle h, int32_t kind, int64_t ticket, int64_t param, int64_t param2)
+{
+    if (!h || kind < FDTD_DEBUG_NONE || kind > FDTD_DEBUG_ORDER) return FDTD_ERR_INVALID_ARG;
+    if (kind == FDTD_DEBUG_DELAY && param <= 0) return FDTD_ERR_INVALID_ARG;
+    if (kind == FDTD_DEBUG_ORDER) {
+        if (param < 0 || param > 2) return FDTD_ERR_INVALID_ARG;
+        if (h->c.scheme != FDTD_SCHEME_SYSTOLIC) return FDTD_OK;
+        return upload_tiles(h, (int)param, (unsigned)ticket);
+    }
+    h->dbg_kind = kind;
+    h->dbg_ticket = ticket;
+    h->dbg_param = param;
+    h->dbg_param2 = param2;
+    return FDTD_OK;
+}
+
+} // extern "C"

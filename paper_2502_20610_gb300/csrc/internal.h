@@ -1,0 +1,60 @@
+// Internal declarations shared by the host API and the kernels of libfdtd.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define FDTD_MAX_SOURCES 16
+
+// Device error word values (ctrl[1]); anything non-zero stops every CTA.
+enum : int { DEV_OK = 0, DEV_ERR_TIMEOUT = 1 };
+
+// A point source as the kernels see it: E component `comp` of cell
+// (i,j,k) receives amp[n] after the E half-step of absolute step n < n_amp.
+struct SrcDesc {
+    int comp, i, j, k;
+    long long idx;
+    long long n_amp;
+    const float *amp;
+};
+
+struct SrcSet {
+    int n;
+    SrcDesc s[FDTD_MAX_SOURCES];
+};
+
+// Naive scheme: one H launch and one E launch per step.
+cudaError_t launch_naive_h(float *const f[6], int nx, int ny, int nz, float neg_dt,
+                           cudaStream_t st);
+cudaError_t launch_naive_e(float *const f[6], const float *ce, int nx, int ny, int nz,
+                           long long step, const SrcSet &src, cudaStream_t st);
+
+// Systolic scheme: subdomain ("tile") geometry is fixed at compile time:
+// a ring of RX x RY x RZ cells per CTA, of which (RX-1)(RY-1)(RZ-1) are
+// updated per step (the paper's 31 x 15 x 15 updated, 32 x 16 x 16 stored).
+constexpr int SYS_RX = 32, SYS_RY = 16, SYS_RZ = 16;
+constexpr int SYS_NX = SYS_RX - 1, SYS_NY = SYS_RY - 1, SYS_NZ = SYS_RZ - 1;
+
+struct SysLaunch {
+    float *f[6];
+    const float *ce;
+    int nx, ny, nz;
+    int gx, gy, gz;          // tile grid over skewed space sigma = p + t
+    int T;                   // steps of this launch
+    unsigned epoch;          // progress values of this launch are epoch + k
+    long long step0;         // absolute step at launch start
+    const int *tiles;        // ticket -> linear tile id, topological order
+    int ntiles;
+    unsigned *progress;      // per linear tile id
+    int *ctrl;               // [0] ticket counter, [1] error word, [2..] error info
+    float neg_dt;
+    long long timeout_ns;
+    int dbg_kind;
+    long long dbg_ticket, dbg_param, dbg_param2;
+    SrcSet src;
+};
+
+size_t systolic_smem_bytes();
+cudaError_t systolic_configure();
+int systolic_max_ctas_per_sm();
+cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st);

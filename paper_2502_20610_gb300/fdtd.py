@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libfdtd (include/fdtd.h).
+
+Argument marshalling only: every step of the update runs in the library's
+CUDA kernels.  PyTorch supplies the device workspace and the stream.
+There is no CPU fallback: if libfdtd.so is missing, creating a simulation
+raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfdtd.so")
+
+FDTD_OK, FDTD_ERR_INVALID_ARG, FDTD_ERR_UNSUPPORTED, FDTD_ERR_OOM, FDTD_ERR_CUDA, \
+    FDTD_ERR_TIMEOUT, FDTD_ERR_STATE = range(7)
+SCHEMES = {"naive": 0, "systolic": 1}
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+BOUNDARY = {"pec": 0, "graded": 1, "learned": 2}
+DEBUG_NONE, DEBUG_SKIP_PUBLISH, DEBUG_DELAY, DEBUG_ORDER = range(4)
+
+#: every symbol include/fdtd.h declares
+EXPORTS = ("fdtd_workspace_size", "fdtd_create", "fdtd_add_source", "fdtd_write_fields",
+           "fdtd_step", "fdtd_read_fields", "fdtd_sync", "fdtd_current_step",
+           "fdtd_set_current_step", "fdtd_launch_count", "fdtd_status_string", "fdtd_destroy",
+           "fdtd_debug_set")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class Coeffs(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("scheme", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("field_scale", ctypes.c_float * 6), ("tile", ctypes.c_int32 * 3),
+                ("cluster", ctypes.c_int32 * 3), ("wait_timeout_s", ctypes.c_double),
+                ("max_source_steps", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32)]
+
+
+class Boundary(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("thickness", ctypes.c_int32), ("sigma_max", ctypes.c_double),
+                ("poly_order", ctypes.c_int32), ("model", ctypes.c_void_p)]
+
+
+class FdtdError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libfdtd.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    st = ctypes.c_int
+    lib.fdtd_workspace_size.restype = st
+    lib.fdtd_workspace_size.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.fdtd_create.restype = st
+    lib.fdtd_create.argtypes = [P, P, P, P, P, ctypes.c_size_t, P, ctypes.POINTER(P)]
+    lib.fdtd_add_source.restype = st
+    lib.fdtd_add_source.argtypes = [P, I32, I32, I32, I32, P, I64]
+    lib.fdtd_write_fields.restype = st
+    lib.fdtd_write_fields.argtypes = [P, P]
+    lib.fdtd_step.restype = st
+    lib.fdtd_step.argtypes = [P, I64]
+    lib.fdtd_read_fields.restype = st
+    lib.fdtd_read_fields.argtypes = [P, U32, P]
+    lib.fdtd_sync.restype = st
+    lib.fdtd_sync.argtypes = [P]
+    lib.fdtd_current_step.restype = I64
+    lib.fdtd_current_step.argtypes = [P]
+    lib.fdtd_set_current_step.restype = st
+    lib.fdtd_set_current_step.argtypes = [P, I64]
+    lib.fdtd_launch_count.restype = I64
+    lib.fdtd_launch_count.argtypes = [P]
+    lib.fdtd_status_string.restype = ctypes.c_char_p
+    lib.fdtd_status_string.argtypes = [st]
+    lib.fdtd_destroy.restype = None
+    lib.fdtd_destroy.argtypes = [P]
+    lib.fdtd_debug_set.restype = st
+    lib.fdtd_debug_set.argtypes = [P, I32, I64, I64, I64]
+    _lib = lib
+    return lib
+
+
+def status_string(s):
+    if _lib is None:
+        return {0: "ok", 1: "invalid argument", 2: "unsupported option", 3: "workspace too small",
+                4: "CUDA error", 5: "device wait timed out", 6: "invalid state"}.get(s, "unknown")
+    return _lib.fdtd_status_string(s).decode()
+
+
+def _check(status, what):
+    if status != FDTD_OK:
+        raise FdtdError(status, what)
+
+
+def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
+                steps_per_launch=0, max_source_steps=0, boundary="pec"):
+    nz, ny, nx = (int(s) for s in shape_zyx)
+    g = Grid(nx, ny, nz)
+    c = Coeffs()
+    c.dt = float(dt)
+    c.scheme = SCHEMES[scheme]
+    c.storage = STORAGE[storage]
+    for a in range(6):
+        c.field_scale[a] = 1.0
+    c.wait_timeout_s = float(timeout_s)
+    c.steps_per_launch = int(steps_per_launch)
+    c.max_source_steps = int(max_source_steps)
+    b = Boundary()
+    b.kind = BOUNDARY[boundary]
+    return g, c, b
+
+
+def workspace_size(shape_zyx, dt, **kw):
+    lib = load_library()
+    g, c, b = make_params(shape_zyx, dt, **kw)
+    n = ctypes.c_size_t(0)
+    _check(lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c), ctypes.byref(b), ctypes.byref(n)),
+           "fdtd_workspace_size")
+    return int(n.value)
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (contiguous)."""
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return x.ctypes.data
+
+
+class Sim:
+    """One simulation: (nz, ny, nx) grid, per-cell eps, PEC box.
+
+    scheme: "naive" (one kernel per half-step) or "systolic" (persistent
+    skewed-tile kernel).  Fields are exchanged as float32 (6, nz, ny, nx)
+    arrays in component order Ex, Ey, Ez, Hx, Hy, Hz.
+    """
+
+    def __init__(self, shape_zyx, eps, dt, scheme="systolic", device=None, timeout_s=2.0,
+                 steps_per_launch=0, max_source_steps=0):
+        import torch
+        self._lib = load_library()
+        self.shape = tuple(int(s) for s in shape_zyx)
+        self.dt = float(dt)
+        self.scheme = scheme
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        g, c, b = make_params(self.shape, dt, scheme=scheme, timeout_s=timeout_s,
+                              steps_per_launch=steps_per_launch, max_source_steps=max_source_steps)
+        self._params = (g, c, b)
+        n = ctypes.c_size_t(0)
+        _check(self._lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c), ctypes.byref(b),
+                                             ctypes.byref(n)), "fdtd_workspace_size")
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(int(n.value), dtype=torch.uint8, device=self.device)
+            self.stream = torch.cuda.current_stream(self.device)
+        eps = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), self.shape))
+        h = ctypes.c_void_p(0)
+        with torch.cuda.device(self.device):
+            _check(self._lib.fdtd_create(ctypes.byref(g), eps.ctypes.data, ctypes.byref(c), ctypes.byref(b),
+                                         self.workspace.data_ptr(), int(n.value),
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+                   "fdtd_create")
+        self._h = h
+
+    @property
+    def ncell(self):
+        nz, ny, nx = self.shape
+        return nz * ny * nx
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.fdtd_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_source(self, component, i, j, k, J):
+        J = np.ascontiguousarray(np.asarray(J, dtype=np.float64))
+        _check(self._lib.fdtd_add_source(self._h, int(component), int(i), int(j), int(k), J.ctypes.data,
+                                         J.size), "fdtd_add_source")
+
+    def write_fields(self, fields):
+        """fields: float32 (6, nz, ny, nx), torch tensor (any device) or numpy."""
+        import torch
+        if isinstance(fields, np.ndarray):
+            fields = torch.from_numpy(np.ascontiguousarray(fields, dtype=np.float32))
+        if fields.dtype != torch.float32 or tuple(fields.shape) != (6,) + self.shape:
+            raise ValueError(f"expected float32 {(6,) + self.shape}, got {fields.dtype} {tuple(fields.shape)}")
+        fields = fields.contiguous()
+        self._keep = fields  # the copy is asynchronous
+        _check(self._lib.fdtd_write_fields(self._h, _ptr(fields)), "fdtd_write_fields")
+        if fields.device.type == "cpu":
+            self.sync()
+
+    def write_fields_ptr(self, ptr):
+        _check(self._lib.fdtd_write_fields(self._h, ctypes.c_void_p(ptr)), "fdtd_write_fields")
+
+    def step(self, n):
+        _check(self._lib.fdtd_step(self._h, int(n)), "fdtd_step")
+
+    def sync(self):
+        _check(self._lib.fdtd_sync(self._h), "fdtd_sync")
+
+    def read_fields(self, mask=0x3F, out=None):
+        """Components in `mask` as a float32 (k, nz, ny, nx) tensor (device by default)."""
+        import torch
+        k = bin(mask & 0x3F).count("1")
+        if out is None:
+            out = torch.empty((k,) + self.shape, dtype=torch.float32, device=self.device)
+        _check(self._lib.fdtd_read_fields(self._h, int(mask), ctypes.c_void_p(_ptr(out))), "fdtd_read_fields")
+        return out
+
+    def read_fields_ptr(self, mask, ptr):
+        _check(self._lib.fdtd_read_fields(self._h, int(mask), ctypes.c_void_p(ptr)), "fdtd_read_fields")
+
+    @property
+    def current_step(self):
+        return int(self._lib.fdtd_current_step(self._h))
+
+    def set_current_step(self, s):
+        _check(self._lib.fdtd_set_current_step(self._h, int(s)), "fdtd_set_current_step")
+
+    @property
+    def launch_count(self):
+        return int(self._lib.fdtd_launch_count(self._h))
+
+    def debug_set(self, kind, ticket=0, param=0, param2=0):
+        _check(self._lib.fdtd_debug_set(self._h, int(kind), int(ticket), int(param), int(param2)),
+               "fdtd_debug_set")

@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every symbol include/fdtd.h
+declares; host-side argument checks (no GPU compute)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2502_20610_gb300 import build as libbuild
+from paper_2502_20610_gb300 import fdtd
+from paper_2502_20610_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return fdtd.load_library()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "fdtd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdtd_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(fdtd.EXPORTS) == names
+
+
+def test_workspace_size_and_argument_checks(lib):
+    g, c, b = fdtd.make_params((32, 48, 64), wl.DT_DEFAULT, scheme="systolic")
+    n = ctypes.c_size_t(0)
+    assert lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c), ctypes.byref(b), ctypes.byref(n)) == 0
+    assert n.value >= 7 * 32 * 48 * 64 * 4
+    gn, cn, bn = fdtd.make_params((32, 48, 64), wl.DT_DEFAULT, scheme="naive")
+    m = ctypes.c_size_t(0)
+    assert lib.fdtd_workspace_size(ctypes.byref(gn), ctypes.byref(cn), ctypes.byref(bn), ctypes.byref(m)) == 0
+    assert m.value < n.value  # no tile schedule for the naive scheme
+    bad = fdtd.Grid(0, 4, 4)
+    assert lib.fdtd_workspace_size(ctypes.byref(bad), ctypes.byref(c), ctypes.byref(b),
+                                   ctypes.byref(n)) == fdtd.FDTD_ERR_INVALID_ARG
+    c2 = fdtd.Coeffs.from_buffer_copy(c)
+    c2.dt = -1.0
+    assert lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c2), ctypes.byref(b),
+                                   ctypes.byref(n)) == fdtd.FDTD_ERR_INVALID_ARG
+    b2 = fdtd.Boundary.from_buffer_copy(b)
+    b2.kind = 7
+    assert lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c), ctypes.byref(b2),
+                                   ctypes.byref(n)) == fdtd.FDTD_ERR_INVALID_ARG
+    assert lib.fdtd_workspace_size(None, ctypes.byref(c), ctypes.byref(b), ctypes.byref(n)) == \
+        fdtd.FDTD_ERR_INVALID_ARG
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.fdtd_step(None, 1) == fdtd.FDTD_ERR_INVALID_ARG
+    assert lib.fdtd_current_step(None) == -1
+    assert lib.fdtd_launch_count(None) == -1
+    lib.fdtd_destroy(None)
+    for s in range(7):
+        assert lib.fdtd_status_string(s)
+    assert lib.fdtd_status_string(99) == b"unknown status"
+
+
+def test_product_path_has_no_oracle_import():
+    """The library binding never reaches the oracle (no CPU fallback)."""
+    pkg = os.path.join(ROOT, "paper_2502_20610_gb300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            src = open(os.path.join(pkg, name)).read()
+            assert not re.search(r"^\s*(from|import)\s+oracle", src, flags=re.M), name
+            assert "yee_oracle" not in src, name
