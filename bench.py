@@ -107,9 +107,10 @@ def cpu_baseline(shape, budget_s=15.0):
     eps, J, (c, i, j, k) = make_workload(shape)
     o = YeeOracle(shape, wl.DT_DEFAULT, eps)
     o.add_source(c, i, j, k, J)
+    o.step(1)  # first touch of the arrays
     t0 = time.perf_counter()
-    o.step(1)
-    t1 = time.perf_counter() - t0
+    o.step(2)
+    t1 = (time.perf_counter() - t0) / 2
     n = max(1, min(STEPS_PER_CALL, int(budget_s / max(t1, 1e-6))))
     t0 = time.perf_counter()
     o.step(n)
@@ -148,22 +149,48 @@ def barrier(world):
 
 
 def run_reference(args, world, rank):
+    """Reference arm: the FP64 CPU oracle as it stands, on this host's cores.
+    Each of the W warm-up and K timed steps advances the same workload by a
+    bounded number of oracle steps (the sample), so the run stays within a
+    few minutes; the value is cell updates per second of the timed steps."""
     if rank != 0:
         return 0
-    cb = cpu_baseline(GRID, budget_s=float(os.environ.get("BENCH_CPU_BUDGET_S", "15")))
-    line = {"impl": "reference", "metric": "GCUPS of 3D Yee update (FP64 CPU oracle)",
-            "value": cb["value"], "unit": "GCUPS", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": workload_config(),
-            "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    from oracle import YeeOracle
+    from paper_2502_20610_gb300 import workloads as wl
+    shape = GRID
+    eps, J, (c, i, j, k) = make_workload(shape)
+    o = YeeOracle(shape, wl.DT_DEFAULT, eps)
+    o.add_source(c, i, j, k, J)
+    o.step(1)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    budget = float(os.environ.get("BENCH_CPU_BUDGET_S", "60"))
+    n = max(1, min(STEPS_PER_CALL, int(budget / max(args.steps + args.warmup, 1) / max(t1, 1e-6))))
+    for _ in range(args.warmup):
+        o.step(n)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(n)
+    el = time.perf_counter() - t0
+    cells = shape[0] * shape[1] * shape[2]
+    v = cells * n * args.steps / el / 1e9
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cb = {"value": v, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+          "sample": f"each step: {n} oracle steps (of {STEPS_PER_CALL}) of the same workload, FP64"}
+    line = {"impl": "reference", "metric": "GCUPS of 3D Yee update, systolic vs naive kernel, FP32 & FP16-stored, 1 GB300",
+            "value": v, "unit": "GCUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def workload_config():
-    return {"workload": "256^3 Si/SiO2 eps map (seed 1), PEC walls, Jz dipole lambda=20 at the centre, "
-                        "2000 steps per call, FP32 fields",
+    return {"workload": f"{GRID[0]}^3 Si/SiO2 eps map (seed 1), PEC walls, Jz dipole lambda=20 at the "
+                        f"centre, {STEPS_PER_CALL} steps per call, FP32 fields",
             "grid_xyz": list(GRID[::-1]), "steps_per_call": STEPS_PER_CALL,
             "l2": "inputs larger than L2 (470 MB device state), no flush",
             "parallelism": "replicas (one independent simulation per GPU)"}
@@ -183,6 +210,7 @@ def time_calls(sim, n_calls, stream):
 
 
 def main():
+    global GRID, STEPS_PER_CALL
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -191,7 +219,12 @@ def main():
     ap.add_argument("--naive-calls", type=int, default=1, help="timed naive calls (context)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grid", type=int, default=GRID[0], help="cubic grid edge (profiling runs)")
+    ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
+    ap.add_argument("--scheme", default="systolic", choices=["systolic", "naive"])
     args = ap.parse_args()
+    GRID = (args.grid,) * 3
+    STEPS_PER_CALL = args.steps_per_call
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
@@ -207,7 +240,7 @@ def main():
     cells = shape[0] * shape[1] * shape[2]
     eps, J, (c, i, j, k) = make_workload(shape)
 
-    sim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme="systolic", device=device,
+    sim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme=args.scheme, device=device,
                    steps_per_launch=STEPS_PER_CALL, max_source_steps=J.size)
     sim.add_source(c, i, j, k, J)
     for _ in range(args.warmup):
@@ -274,7 +307,7 @@ def main():
         "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(),
-        "scheme": "systolic",
+        "scheme": args.scheme,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                      "kernel": "systolic_kernel",

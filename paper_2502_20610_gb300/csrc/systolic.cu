@@ -54,12 +54,11 @@ static_assert(SHELL == VOL - TX * TY * TZ, "shell enumeration");
 static_assert(TOP == TX * TY * TZ - (TX - 1) * (TY - 1) * (TZ - 1), "top-face enumeration");
 
 // Shared-memory slot of ring position (sx, sy, sz).  Rows of 32 x-slots are
-// rotated by their row index, so a warp reading one row, or reading one
-// x-slot of 32 consecutive rows, touches 32 distinct banks.
+// rotated by sy, so a warp reading one row, or reading one x-slot across the
+// y-slots, touches distinct banks; the rotation is a per-thread constant.
 __device__ __forceinline__ int slot(int sx, int sy, int sz)
 {
-    const int row = sz * RY + sy;
-    return (row << 5) | ((sx + row) & 31);
+    return ((sz * RY + sy) << 5) | ((sx + sy) & 31);
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -108,47 +107,60 @@ __device__ __forceinline__ Interval tile_interval(const SysLaunch &P, int I, int
     return r;
 }
 
-// Bounded spin on one flag.  Returns false if the launch is aborting.
-__device__ bool wait_flag(const SysLaunch &P, const unsigned *flag, unsigned target, int ticket)
-{
-    unsigned long long t0 = 0;
-    for (int it = 0;; ++it) {
-        if (ld_acquire(flag) >= target) return true;
-        if (ld_volatile(P.ctrl + 1) != DEV_OK) return false;
-        const unsigned long long now = globaltimer();
-        if (it == 0) {
-            t0 = now;
-        } else if (now - t0 > (unsigned long long)P.timeout_ns) {
-            if (atomicCAS(P.ctrl + 1, DEV_OK, DEV_ERR_TIMEOUT) == DEV_OK) {
-                P.ctrl[2] = ticket;
-                P.ctrl[3] = (int)target;
-            }
-            return false;
-        }
-        __nanosleep(it < 64 ? 32 : 256);
-    }
-}
+// Progress flags of the three upwind face neighbours of the current tile,
+// and the last value seen on each (so most steps need no poll at all).
+struct Upwind {
+    int id[3];       // linear tile id, -1 if none
+    int s[3], e[3];  // their active intervals in this launch
+};
 
 // Wait until every -x, -y, -z neighbour that holds state at level L has
 // completed it (progress >= epoch + L + 1).  A neighbour u is waited on if
 // start(u)-1 <= L <= end(u) and start(u) <= end(u)+1: outside that range its
-// cells at level L are outside the domain.  Subdomains that enter the domain
-// at L+1 publish epoch+start(u) after their own initial wait, which carries
-// the guarantee of the tiles behind them.  Thread 0 only.
-__device__ bool wait_upstream(const SysLaunch &P, int I, int J, int K, int L, int ticket)
+// cells at level L lie outside the domain.  A neighbour that enters the
+// domain at L+1 publishes epoch+start(u) after its own initial wait, which
+// carries the guarantee of the tiles behind it.  Lanes 0..2 of warp 0 each
+// watch one neighbour; returns false (in every lane) if the launch aborts.
+__device__ bool wait_level(const SysLaunch &P, const Upwind &U, unsigned *seen, int L, int ticket)
 {
-    if (ld_volatile(P.ctrl + 1) != DEV_OK) return false;
-    const unsigned target = P.epoch + (unsigned)L + 1u;
-    const int nb[3][3] = {{I - 1, J, K}, {I, J - 1, K}, {I, J, K - 1}};
-    for (int a = 0; a < 3; ++a) {
-        const int u0 = nb[a][0], u1 = nb[a][1], u2 = nb[a][2];
-        if (u0 < 0 || u1 < 0 || u2 < 0) continue;
-        const Interval iv = tile_interval(P, u0, u1, u2);
-        if (iv.s > iv.e + 1 || L < iv.s - 1 || L > iv.e) continue;
-        const int id = u0 + P.gx * (u1 + P.gy * u2);
-        if (!wait_flag(P, P.progress + id, target, ticket)) return false;
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    if (lane < 3) {
+        const int a = lane;
+        // select this lane's neighbour without a dynamically indexed array
+        const int id = a == 0 ? U.id[0] : (a == 1 ? U.id[1] : U.id[2]);
+        const int us = a == 0 ? U.s[0] : (a == 1 ? U.s[1] : U.s[2]);
+        const int ue = a == 0 ? U.e[0] : (a == 1 ? U.e[1] : U.e[2]);
+        const unsigned target = P.epoch + (unsigned)L + 1u;
+        if (id >= 0 && us <= ue + 1 && L >= us - 1 && L <= ue && seen[a] < target) {
+            const unsigned *flag = P.progress + id;
+            unsigned long long t0 = 0;
+            for (int it = 0;; ++it) {
+                const unsigned v = ld_acquire(flag);
+                if (v >= target) {
+                    seen[a] = v;
+                    break;
+                }
+                if (ld_volatile(P.ctrl + 1) != DEV_OK) {
+                    ok = false;
+                    break;
+                }
+                const unsigned long long now = globaltimer();
+                if (it == 0) {
+                    t0 = now;
+                } else if (now - t0 > (unsigned long long)P.timeout_ns) {
+                    if (atomicCAS(P.ctrl + 1, DEV_OK, DEV_ERR_TIMEOUT) == DEV_OK) {
+                        P.ctrl[2] = ticket;
+                        P.ctrl[3] = (int)target;
+                    }
+                    ok = false;
+                    break;
+                }
+                __nanosleep(it < 64 ? 32 : 256);
+            }
+        }
     }
-    return true;
+    return __all_sync(0xffffffffu, ok);
 }
 
 __device__ __forceinline__ void publish(const SysLaunch &P, int tile, int ticket, unsigned value)
@@ -156,8 +168,7 @@ __device__ __forceinline__ void publish(const SysLaunch &P, int tile, int ticket
     if (P.dbg_kind == 1 /* skip publish */ && ticket == P.dbg_ticket) return;
     if (P.dbg_kind == 2 /* delay */ && P.dbg_param > 0 && (ticket % P.dbg_param) == P.dbg_ticket)
         __nanosleep((unsigned)P.dbg_param2);
-    __threadfence();
-    st_release(P.progress + tile, value);
+    st_release(P.progress + tile, value);  // release: orders the CTA's stores before the flag
 }
 
 __device__ __forceinline__ bool in_dom(const SysLaunch &P, int x, int y, int z)
@@ -170,24 +181,49 @@ __device__ __forceinline__ long long gidx(const SysLaunch &P, int x, int y, int 
     return x + (long long)P.nx * (y + (long long)P.ny * z);
 }
 
-// Ring slot (sx,sy,sz) of shell entry f in [0, SHELL) for a window whose
-// extra slot is (ex, ey, ez).
-__device__ __forceinline__ void shell_slot(int f, int ex, int ey, int ez, int &sx, int &sy, int &sz)
+// Shell entry f in [0, SHELL): face category and two coordinates inside the
+// face, packed as cat | a << 8 | b << 16 (computed once per thread).
+//   cat 0 (z face): ring sx = a, sy = b
+//   cat 1 (y face, z not extra): ring sx = a, z offset b in [0, RZ-1)
+//   cat 2 (x face only): y offset a, z offset b in [0, RY-1) x [0, RZ-1)
+__device__ __forceinline__ int shell_code(int f)
 {
-    if (f < SHELL_Z) {
-        sx = f & 31; sy = f >> 5; sz = ez;
-    } else if (f < SHELL_Z + SHELL_Y) {
+    if (f >= SHELL) return -1;
+    if (f < SHELL_Z) return 0 | ((f & 31) << 8) | ((f >> 5) << 16);
+    if (f < SHELL_Z + SHELL_Y) {
         const int g = f - SHELL_Z;
-        sx = g & 31; sy = ey; sz = (ez + 1 + (g >> 5)) & (RZ - 1);
-    } else {
-        const int g = f - SHELL_Z - SHELL_Y;
-        sx = ex; sy = (ey + 1 + g % (RY - 1)) & (RY - 1); sz = (ez + 1 + g / (RY - 1)) & (RZ - 1);
+        return 1 | ((g & 31) << 8) | ((g >> 5) << 16);
     }
+    const int g = f - SHELL_Z - SHELL_Y;
+    return 2 | ((g % (RY - 1)) << 8) | ((g / (RY - 1)) << 16);
 }
 
-// Box offsets (dx,dy,dz) of top-face entry f in [0, TOP).
-__device__ __forceinline__ void top_cell(int f, int &dx, int &dy, int &dz)
+// Ring slot and physical cell of a shell entry for the E window of step t,
+// whose lower corner is b - 1 and whose extra ring slot is e = (b-1) mod R.
+__device__ __forceinline__ void shell_cell(int code, int bx, int by, int bz, int &o, int &px, int &py,
+                                           int &pz)
 {
+    const int cat = code & 0xff, a = (code >> 8) & 0xff, b = code >> 16;
+    const int ex = (bx - 1) & 31, ey = (by - 1) & (RY - 1), ez = (bz - 1) & (RZ - 1);
+    int sx, sy, sz;
+    if (cat == 0) {
+        sx = a; sy = b; sz = ez;
+        px = bx - 1 + ((a - bx + 1) & 31); py = by - 1 + ((b - by + 1) & (RY - 1)); pz = bz - 1;
+    } else if (cat == 1) {
+        sx = a; sy = ey; sz = (ez + 1 + b) & (RZ - 1);
+        px = bx - 1 + ((a - bx + 1) & 31); py = by - 1; pz = bz + b;
+    } else {
+        sx = ex; sy = (ey + 1 + a) & (RY - 1); sz = (ez + 1 + b) & (RZ - 1);
+        px = bx - 1; py = by + a; pz = bz + b;
+    }
+    o = slot(sx, sy, sz);
+}
+
+// Top-face entry f in [0, TOP): box offsets packed dx | dy << 8 | dz << 16.
+__device__ __forceinline__ int top_code(int f)
+{
+    if (f >= TOP) return -1;
+    int dx, dy, dz;
     if (f < TOP_Z) {
         dx = f % TX; dy = f / TX; dz = TZ - 1;
     } else if (f < TOP_Z + TOP_Y) {
@@ -197,25 +233,46 @@ __device__ __forceinline__ void top_cell(int f, int &dx, int &dy, int &dz)
         const int g = f - TOP_Z - TOP_Y;
         dx = TX - 1; dy = g % (TY - 1); dz = g / (TY - 1);
     }
+    return dx | (dy << 8) | (dz << 16);
 }
+
+constexpr int TOP_PT = (TOP + NTHREADS - 1) / NTHREADS;
+constexpr int ZS = RY * 32;  // floats between consecutive z rows of the ring
 
 __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P)
 {
     extern __shared__ float smem[];
-    float *const sF[6] = {smem, smem + VOL, smem + 2 * VOL, smem + 3 * VOL, smem + 4 * VOL,
-                          smem + 5 * VOL};
+    float *const sEx = smem, *const sEy = smem + VOL, *const sEz = smem + 2 * VOL;
+    float *const sHx = smem + 3 * VOL, *const sHy = smem + 4 * VOL, *const sHz = smem + 5 * VOL;
     float *const sCE = smem + 6 * VOL;
+    float *const sF[6] = {sEx, sEy, sEz, sHx, sHy, sHz};
     __shared__ int s_ticket, s_abort;
+    __shared__ unsigned s_seen[3];
 
     const int tid = threadIdx.x;
     const int sx = tid & 31, sy = tid >> 5;
+    const int warp = tid >> 5;
     const float ndt = P.neg_dt;
+
+    // per-thread constant ring offsets of the column and its x/y neighbours
+    const int syp = (sy + 1) & (RY - 1), sym = (sy - 1) & (RY - 1);
+    const int o_s = (sy << 5) | ((sx + sy) & 31);
+    const int o_xp = (sy << 5) | ((sx + 1 + sy) & 31);
+    const int o_xm = (sy << 5) | ((sx - 1 + sy) & 31);
+    const int o_yp = (syp << 5) | ((sx + syp) & 31);
+    const int o_ym = (sym << 5) | ((sx + sym) & 31);
+    int sh_code[SHELL_PT], tp_code[TOP_PT];
+#pragma unroll
+    for (int q = 0; q < SHELL_PT; ++q) sh_code[q] = shell_code(tid + q * NTHREADS);
+#pragma unroll
+    for (int q = 0; q < TOP_PT; ++q) tp_code[q] = top_code(tid + q * NTHREADS);
 
     for (;;) {
         if (tid == 0) {
             s_ticket = atomicAdd(P.ctrl, 1);
             s_abort = ld_volatile(P.ctrl + 1) != DEV_OK;
         }
+        if (tid < 3) s_seen[tid] = 0u;
         __syncthreads();
         const int ticket = s_ticket;
         const bool stop = s_abort || ticket >= P.ntiles;
@@ -225,9 +282,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
         const int I = tile % P.gx, J = (tile / P.gx) % P.gy, K = tile / (P.gx * P.gy);
         const int Ax = I * TX, Ay = J * TY, Az = K * TZ;
         const Interval iv = tile_interval(P, I, J, K);
+        Upwind U;
+        {
+            const int nb[3][3] = {{I - 1, J, K}, {I, J - 1, K}, {I, J, K - 1}};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (nb[a][0] < 0 || nb[a][1] < 0 || nb[a][2] < 0) {
+                    U.id[a] = -1; U.s[a] = 1; U.e[a] = -1;
+                } else {
+                    const Interval u = tile_interval(P, nb[a][0], nb[a][1], nb[a][2]);
+                    U.id[a] = nb[a][0] + P.gx * (nb[a][1] + P.gy * nb[a][2]);
+                    U.s[a] = u.s; U.e[a] = u.e;
+                }
+            }
+        }
 
         if (iv.s > 0) {
-            if (tid == 0) s_abort = !wait_upstream(P, I, J, K, iv.s - 1, ticket);
+            if (warp == 0) {
+                const bool ok = wait_level(P, U, s_seen, iv.s - 1, ticket);
+                if (tid == 0) s_abort = !ok;
+            }
             __syncthreads();
             if (s_abort) break;
         }
@@ -243,7 +317,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
             const int px = bx + ((sx - bx) & 31), py = by + ((sy - by) & (RY - 1));
             for (int sz = 0; sz < RZ; ++sz) {
                 const int pz = bz + ((sz - bz) & (RZ - 1));
-                const int o = slot(sx, sy, sz);
+                const int o = sz * ZS + o_s;
                 if (in_dom(P, px, py, pz)) {
                     const long long g = gidx(P, px, py, pz);
 #pragma unroll
@@ -257,29 +331,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
             }
         }
         __syncthreads();
-        if (iv.s > 0 && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.s);
+        if (warp == 0) {
+            if (iv.s > 0 && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.s);
+            const bool ok = wait_level(P, U, s_seen, iv.s, ticket);
+            if (tid == 0) s_abort = !ok;
+        }
+        __syncthreads();
+        if (s_abort) break;
 
         bool abort = false;
         for (int t = iv.s; t <= iv.e; ++t) {
             const int bx = Ax - t, by = Ay - t, bz = Az - t;  // box low corner at step t
-            const int ex = (bx - 1) & 31, ey = (by - 1) & (RY - 1), ez = (bz - 1) & (RZ - 1);
 
-            // 1. upstream neighbours have finished step t
-            if (tid == 0) s_abort = !wait_upstream(P, I, J, K, t, ticket);
-            __syncthreads();
-            if (s_abort) { abort = true; break; }
-
-            // 2. lower shell (level t) into registers
+            // 1. lower shell (level t; upwind neighbours are done) into registers
             float shv[SHELL_PT][7];
+            int sho[SHELL_PT];
 #pragma unroll
             for (int q = 0; q < SHELL_PT; ++q) {
-                const int f = tid + q * NTHREADS;
-                if (f < SHELL) {
-                    int qx, qy, qz;
-                    shell_slot(f, ex, ey, ez, qx, qy, qz);
-                    const int px = (bx - 1) + ((qx - bx + 1) & 31);
-                    const int py = (by - 1) + ((qy - by + 1) & (RY - 1));
-                    const int pz = (bz - 1) + ((qz - bz + 1) & (RZ - 1));
+                sho[q] = -1;
+                if (sh_code[q] >= 0) {
+                    int px, py, pz;
+                    shell_cell(sh_code[q], bx, by, bz, sho[q], px, py, pz);
                     if (in_dom(P, px, py, pz)) {
                         const long long g = gidx(P, px, py, pz);
 #pragma unroll
@@ -292,71 +364,63 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
                 }
             }
 
-            // this thread's (x,y) column of the box
+            // this thread's (x,y) column of the box and its z range in the domain
             const int dxc = (sx - bx) & 31, dyc = (sy - by) & (RY - 1);
             const int px = bx + dxc, py = by + dyc;
             const bool col = dxc < TX && dyc < TY && (unsigned)px < (unsigned)P.nx &&
                              (unsigned)py < (unsigned)P.ny;
-            const int sxp = (sx + 1) & 31, syp = (sy + 1) & (RY - 1);
-            const int sxm = (sx - 1) & 31, sym = (sy - 1) & (RY - 1);
+            const int dz_lo = max(0, -bz), dz_hi = min(TZ, P.nz - bz);
+            const int r0 = bz & (RZ - 1);
 
-            // 3. H half-step on the box
+            // 2. H half-step on the box
             if (col) {
-                int r = bz & (RZ - 1);
-                float exc = sF[0][slot(sx, sy, r)], eyc = sF[1][slot(sx, sy, r)];
+                float exc = sEx[r0 * ZS + o_s], eyc = sEy[r0 * ZS + o_s];
+#pragma unroll
                 for (int dz = 0; dz < TZ; ++dz) {
-                    const int rn = (r + 1) & (RZ - 1);
-                    const float exn = sF[0][slot(sx, sy, rn)], eyn = sF[1][slot(sx, sy, rn)];
-                    const int pz = bz + dz;
-                    if ((unsigned)pz < (unsigned)P.nz) {
-                        const int o = slot(sx, sy, r);
-                        const float ez = sF[2][o];
-                        const int oxp = slot(sxp, sy, r), oyp = slot(sx, syp, r);
-                        sF[3][o] = h_x(sF[3][o], sF[2][oyp], ez, eyn, eyc, ndt);
-                        sF[4][o] = h_y(sF[4][o], exn, exc, sF[2][oxp], ez, ndt);
-                        sF[5][o] = h_z(sF[5][o], sF[1][oxp], eyc, sF[0][oyp], exc, ndt);
+                    const int rb = ((r0 + dz) & (RZ - 1)) * ZS;
+                    const int rn = ((r0 + dz + 1) & (RZ - 1)) * ZS;
+                    const float exn = sEx[rn + o_s], eyn = sEy[rn + o_s];
+                    if (dz >= dz_lo && dz < dz_hi) {
+                        const float ez = sEz[rb + o_s];
+                        sHx[rb + o_s] = h_x(sHx[rb + o_s], sEz[rb + o_yp], ez, eyn, eyc, ndt);
+                        sHy[rb + o_s] = h_y(sHy[rb + o_s], exn, exc, sEz[rb + o_xp], ez, ndt);
+                        sHz[rb + o_s] = h_z(sHz[rb + o_s], sEy[rb + o_xp], eyc, sEx[rb + o_yp], exc, ndt);
                     }
                     exc = exn;
                     eyc = eyn;
-                    r = rn;
                 }
             }
             __syncthreads();
 
-            // 4. shell into the slots of the trailing top layer
+            // 3. shell into the slots of the trailing top layer
 #pragma unroll
             for (int q = 0; q < SHELL_PT; ++q) {
-                const int f = tid + q * NTHREADS;
-                if (f < SHELL) {
-                    int qx, qy, qz;
-                    shell_slot(f, ex, ey, ez, qx, qy, qz);
-                    const int o = slot(qx, qy, qz);
+                if (sho[q] >= 0) {
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) sF[c][o] = shv[q][c];
-                    sCE[o] = shv[q][6];
+                    for (int c = 0; c < 6; ++c) sF[c][sho[q]] = shv[q][c];
+                    sCE[sho[q]] = shv[q][6];
                 }
             }
             __syncthreads();
 
-            // 5. E half-step on the box; PEC: tangential E on low planes fixed
+            // 4. E half-step on the box; PEC: tangential E on low planes fixed
             if (col) {
-                int r = bz & (RZ - 1);
-                const int rm0 = (r - 1) & (RZ - 1);
-                float hxm = sF[3][slot(sx, sy, rm0)], hym = sF[4][slot(sx, sy, rm0)];
+                const int rm = ((r0 - 1) & (RZ - 1)) * ZS;
+                float hxm = sHx[rm + o_s], hym = sHy[rm + o_s];
+                const bool ux = py > 0, uy = px > 0, uz = px > 0 && py > 0;
+#pragma unroll
                 for (int dz = 0; dz < TZ; ++dz) {
-                    const int o = slot(sx, sy, r);
-                    const float hx = sF[3][o], hy = sF[4][o];
-                    const int pz = bz + dz;
-                    if ((unsigned)pz < (unsigned)P.nz) {
-                        const float hz = sF[5][o], ce = sCE[o];
-                        const int oxm = slot(sxm, sy, r), oym = slot(sx, sym, r);
-                        if (py > 0 && pz > 0) sF[0][o] = e_x(sF[0][o], hz, sF[5][oym], hy, hym, ce);
-                        if (px > 0 && pz > 0) sF[1][o] = e_y(sF[1][o], hx, hxm, hz, sF[5][oxm], ce);
-                        if (px > 0 && py > 0) sF[2][o] = e_z(sF[2][o], hy, sF[4][oxm], hx, sF[3][oym], ce);
+                    const int rb = ((r0 + dz) & (RZ - 1)) * ZS;
+                    const float hx = sHx[rb + o_s], hy = sHy[rb + o_s];
+                    if (dz >= dz_lo && dz < dz_hi) {
+                        const float hz = sHz[rb + o_s], ce = sCE[rb + o_s];
+                        const bool kz = bz + dz > 0;
+                        if (ux && kz) sEx[rb + o_s] = e_x(sEx[rb + o_s], hz, sHz[rb + o_ym], hy, hym, ce);
+                        if (uy && kz) sEy[rb + o_s] = e_y(sEy[rb + o_s], hx, hxm, hz, sHz[rb + o_xm], ce);
+                        if (uz) sEz[rb + o_s] = e_z(sEz[rb + o_s], hy, sHy[rb + o_xm], hx, sHx[rb + o_ym], ce);
                     }
                     hxm = hx;
                     hym = hy;
-                    r = (r + 1) & (RZ - 1);
                 }
             }
             __syncthreads();
@@ -385,35 +449,42 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
                 }
             }
 
-            // 6. top faces (or, on the last step of the launch, the whole box)
+            // 5. warp 0 waits for the upwind neighbours' next level while
+            //    everyone stores the top faces (or, on the launch's last
+            //    step, the whole box)
+            bool ok = true;
+            if (warp == 0 && t < iv.e) ok = wait_level(P, U, s_seen, t + 1, ticket);
             if (t == P.T - 1) {
                 if (col) {
-                    for (int dz = 0; dz < TZ; ++dz) {
+                    for (int dz = dz_lo; dz < dz_hi; ++dz) {
                         const int pz = bz + dz;
-                        if ((unsigned)pz < (unsigned)P.nz) {
-                            const int o = slot(sx, sy, pz & (RZ - 1));
-                            const long long g = gidx(P, px, py, pz);
+                        const int o = (pz & (RZ - 1)) * ZS + o_s;
+                        const long long g = gidx(P, px, py, pz);
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) P.f[c][g] = sF[c][o];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < TOP_PT; ++q) {
+                    const int code = tp_code[q];
+                    if (code >= 0) {
+                        const int qx = bx + (code & 0xff), qy = by + ((code >> 8) & 0xff),
+                                  qz = bz + (code >> 16);
+                        if (in_dom(P, qx, qy, qz)) {
+                            const int o = slot(qx & 31, qy & (RY - 1), qz & (RZ - 1));
+                            const long long g = gidx(P, qx, qy, qz);
 #pragma unroll
                             for (int c = 0; c < 6; ++c) P.f[c][g] = sF[c][o];
                         }
                     }
                 }
-            } else {
-                for (int f = tid; f < TOP; f += NTHREADS) {
-                    int dx, dy, dz;
-                    top_cell(f, dx, dy, dz);
-                    const int qx = bx + dx, qy = by + dy, qz = bz + dz;
-                    if (in_dom(P, qx, qy, qz)) {
-                        const int o = slot(qx & 31, qy & (RY - 1), qz & (RZ - 1));
-                        const long long g = gidx(P, qx, qy, qz);
-#pragma unroll
-                        for (int c = 0; c < 6; ++c) P.f[c][g] = sF[c][o];
-                    }
-                }
             }
+            if (tid == 0) s_abort = !ok;
             __syncthreads();
+            if (s_abort) { abort = true; break; }
 
-            // 7. release progress
+            // 6. release progress (the other warps move on to the next step)
             if (tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)t + 1u);
         }
         if (abort) break;
