@@ -222,6 +222,7 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID[0], help="cubic grid edge (profiling runs)")
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
     ap.add_argument("--scheme", default="systolic", choices=["systolic", "naive"])
+    ap.add_argument("--tile", default=None, help="systolic tile shape, e.g. 31x15x15 (default: library's)")
     args = ap.parse_args()
     GRID = (args.grid,) * 3
     STEPS_PER_CALL = args.steps_per_call
@@ -241,7 +242,7 @@ def main():
     eps, J, (c, i, j, k) = make_workload(shape)
 
     sim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme=args.scheme, device=device,
-                   steps_per_launch=STEPS_PER_CALL, max_source_steps=J.size)
+                   steps_per_launch=STEPS_PER_CALL, max_source_steps=J.size, tile=args.tile)
     sim.add_source(c, i, j, k, J)
     for _ in range(args.warmup):
         sim.step(STEPS_PER_CALL)

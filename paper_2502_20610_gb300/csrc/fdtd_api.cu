@@ -22,12 +22,26 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     size_t fields[6], ce, src, progress, tiles, ctrl, total;
+    int variant, tx, ty, tz;  // systolic tile shape
     int gx, gy, gz;
     long long ntiles_max;
     int source_steps, steps_per_launch;
 };
 
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+constexpr int DEFAULT_VARIANT = 0;  // 31 x 15 x 15 measured faster than 31 x 7 x 15 (104 vs 79 GCUPS)
+
+// Tile shape requested in coeffs.tile (0,0,0 = default) -> variant, or -1.
+int pick_variant(const fdtd_coeffs &c)
+{
+    if (c.tile[0] == 0 && c.tile[1] == 0 && c.tile[2] == 0) return DEFAULT_VARIANT;
+    for (int v = 0; v < SYS_NSHAPES; ++v) {
+        const SysShape sh = systolic_shape(v);
+        if (c.tile[0] == sh.tx && c.tile[1] == sh.ty && c.tile[2] == sh.tz) return v;
+    }
+    return -1;
+}
 
 // Everything lives in the caller's workspace:
 //   6 FP32 field arrays, the FP32 coefficient dt/eps, the source tables,
@@ -48,11 +62,17 @@ bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, Layout &L)
     L.steps_per_launch = c.steps_per_launch > 0 ? c.steps_per_launch : DEFAULT_STEPS_PER_LAUNCH;
     L.gx = L.gy = L.gz = 0;
     L.ntiles_max = 0;
+    L.variant = pick_variant(c);
+    if (L.variant < 0) return false;
+    const SysShape sh = systolic_shape(L.variant);
+    L.tx = sh.tx;
+    L.ty = sh.ty;
+    L.tz = sh.tz;
     if (c.scheme == FDTD_SCHEME_SYSTOLIC) {
         const long long T = L.steps_per_launch;
-        L.gx = ceil_div(g.nx + T - 1, SYS_NX);
-        L.gy = ceil_div(g.ny + T - 1, SYS_NY);
-        L.gz = ceil_div(g.nz + T - 1, SYS_NZ);
+        L.gx = ceil_div(g.nx + T - 1, L.tx);
+        L.gy = ceil_div(g.ny + T - 1, L.ty);
+        L.gz = ceil_div(g.nz + T - 1, L.tz);
         L.ntiles_max = (long long)L.gx * L.gy * L.gz;
         if (L.ntiles_max > (1ll << 31) - 1) return false;
     }
@@ -78,11 +98,9 @@ fdtd_status check_args(const fdtd_grid *g, const fdtd_coeffs *c, const fdtd_boun
     for (int a = 0; a < 3; ++a) {
         if (c->tile[a] < 0 || c->cluster[a] < 0) return FDTD_ERR_INVALID_ARG;
     }
-    const int tdef[3] = {SYS_NX, SYS_NY, SYS_NZ};
-    for (int a = 0; a < 3; ++a) {
-        if (c->tile[a] != 0 && c->tile[a] != tdef[a]) return FDTD_ERR_UNSUPPORTED;
+    if (pick_variant(*c) < 0) return FDTD_ERR_UNSUPPORTED;
+    for (int a = 0; a < 3; ++a)
         if (c->cluster[a] > 1) return FDTD_ERR_UNSUPPORTED;
-    }
     if (b->kind < FDTD_BOUNDARY_PEC || b->kind > FDTD_BOUNDARY_LEARNED) return FDTD_ERR_INVALID_ARG;
     if (b->kind != FDTD_BOUNDARY_PEC) return FDTD_ERR_UNSUPPORTED;
     return FDTD_OK;
@@ -109,9 +127,9 @@ void build_tiles(const fdtd_grid &g, const Layout &L, int order, unsigned seed,
     for (int K = 0; K < L.gz; ++K)
         for (int J = 0; J < L.gy; ++J)
             for (int I = 0; I < L.gx; ++I) {
-                const int ax = I * SYS_NX, ay = J * SYS_NY, az = K * SYS_NZ;
+                const int ax = I * L.tx, ay = J * L.ty, az = K * L.tz;
                 const int s = std::max(0, std::max(ax - g.nx + 1, std::max(ay - g.ny + 1, az - g.nz + 1)));
-                const int ge = std::min(ax + SYS_NX - 1, std::min(ay + SYS_NY - 1, az + SYS_NZ - 1));
+                const int ge = std::min(ax + L.tx - 1, std::min(ay + L.ty - 1, az + L.tz - 1));
                 const int e = std::min(T - 1, ge);
                 if (s > e + 1) continue;
                 TileEntry te;
@@ -270,13 +288,13 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     if (e != cudaSuccess) return fail(cuda_status(e));
 
     if (coeffs->scheme == FDTD_SCHEME_SYSTOLIC) {
-        e = systolic_configure();
+        e = systolic_configure(L.variant);
         if (e != cudaSuccess) return fail(cuda_status(e));
         int dev = 0, sms = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return fail(cuda_status(e));
-        const int per_sm = systolic_max_ctas_per_sm();
+        const int per_sm = systolic_max_ctas_per_sm(L.variant);
         if (per_sm < 1) return fail(FDTD_ERR_UNSUPPORTED);
         h->max_ctas = sms * per_sm;
         fdtd_status st = upload_tiles(h, 0, 0);
@@ -373,7 +391,7 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         p.dbg_param2 = h->dbg_param2;
         p.src = h->src;
         const int grid = (int)std::max<long long>(1, std::min<long long>(p.ntiles, h->max_ctas));
-        CK(launch_systolic(p, grid, h->stream));
+        CK(launch_systolic(p, grid, h->stream, h->L.variant));
         h->launches += 1;
         h->epoch += (unsigned)T + 1u;
         h->step += T;

@@ -29,11 +29,14 @@ cudaError_t launch_naive_h(float *const f[6], int nx, int ny, int nz, float neg_
 cudaError_t launch_naive_e(float *const f[6], const float *ce, int nx, int ny, int nz,
                            long long step, const SrcSet &src, cudaStream_t st);
 
-// Systolic scheme: subdomain ("tile") geometry is fixed at compile time:
-// a ring of RX x RY x RZ cells per CTA, of which (RX-1)(RY-1)(RZ-1) are
-// updated per step (the paper's 31 x 15 x 15 updated, 32 x 16 x 16 stored).
-constexpr int SYS_RX = 32, SYS_RY = 16, SYS_RZ = 16;
-constexpr int SYS_NX = SYS_RX - 1, SYS_NY = SYS_RY - 1, SYS_NZ = SYS_RZ - 1;
+// Systolic scheme: the subdomain ("tile") geometry is a compile-time ring of
+// 32 x RY x RZ shared-memory slots per CTA of which 31 x (RY-1) x (RZ-1)
+// cells are updated per step.  Shape 0 is the paper's 31 x 15 x 15 updated /
+// 32 x 16 x 16 stored tile (one CTA per SM); shape 1 is 31 x 7 x 15 (two CTAs
+// per SM, so one hides the other's waits and barriers).
+struct SysShape { int tx, ty, tz; };
+constexpr int SYS_NSHAPES = 2;
+SysShape systolic_shape(int variant);
 
 struct SysLaunch {
     float *f[6];
@@ -54,7 +57,7 @@ struct SysLaunch {
     SrcSet src;
 };
 
-size_t systolic_smem_bytes();
-cudaError_t systolic_configure();
-int systolic_max_ctas_per_sm();
-cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st);
+size_t systolic_smem_bytes(int variant);
+cudaError_t systolic_configure(int variant);
+int systolic_max_ctas_per_sm(int variant);
+cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant);

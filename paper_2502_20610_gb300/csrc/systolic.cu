@@ -35,30 +35,38 @@
 
 namespace {
 
-constexpr int RX = SYS_RX, RY = SYS_RY, RZ = SYS_RZ;
-constexpr int TX = SYS_NX, TY = SYS_NY, TZ = SYS_NZ;
-constexpr int VOL = RX * RY * RZ;
-constexpr int NTHREADS = RX * RY;
-constexpr int SHELL_Z = RX * RY;             // slots with z extra
-constexpr int SHELL_Y = RX * (RZ - 1);       // y extra, z not
-constexpr int SHELL_X = (RY - 1) * (RZ - 1); // x extra only
-constexpr int SHELL = SHELL_Z + SHELL_Y + SHELL_X;
-constexpr int SHELL_PT = (SHELL + NTHREADS - 1) / NTHREADS;
-constexpr int TOP_Z = TX * TY;
-constexpr int TOP_Y = TX * (TZ - 1);
-constexpr int TOP_X = (TY - 1) * (TZ - 1);
-constexpr int TOP = TOP_Z + TOP_Y + TOP_X;
-static_assert(RX == 32, "one warp spans the x ring");
-static_assert((RY & (RY - 1)) == 0 && (RZ & (RZ - 1)) == 0, "ring sizes are powers of two");
-static_assert(SHELL == VOL - TX * TY * TZ, "shell enumeration");
-static_assert(TOP == TX * TY * TZ - (TX - 1) * (TY - 1) * (TZ - 1), "top-face enumeration");
+// Ring geometry: RX x RY x RZ shared-memory slots per tile, (RX-1) x
+// (RY-1) x (RZ-1) cells updated per step, one thread per (x,y) ring column.
+template <int RY_, int RZ_, int MINB_>
+struct Ring {
+    static constexpr int RX = 32, RY = RY_, RZ = RZ_, MINB = MINB_;
+    static constexpr int TX = RX - 1, TY = RY - 1, TZ = RZ - 1;
+    static constexpr int VOL = RX * RY * RZ;
+    static constexpr int NTHREADS = RX * RY;
+    static constexpr int SHELL_Z = RX * RY;             // slots with z extra
+    static constexpr int SHELL_Y = RX * (RZ - 1);       // y extra, z not
+    static constexpr int SHELL_X = (RY - 1) * (RZ - 1); // x extra only
+    static constexpr int SHELL = SHELL_Z + SHELL_Y + SHELL_X;
+    static constexpr int SHELL_PT = (SHELL + NTHREADS - 1) / NTHREADS;
+    static constexpr int TOP_Z = TX * TY;
+    static constexpr int TOP_Y = TX * (TZ - 1);
+    static constexpr int TOP_X = (TY - 1) * (TZ - 1);
+    static constexpr int TOP = TOP_Z + TOP_Y + TOP_X;
+    static constexpr int TOP_PT = (TOP + NTHREADS - 1) / NTHREADS;
+    static constexpr int ZS = RY * 32;  // floats between consecutive z rows of the ring
+    static_assert((RY & (RY - 1)) == 0 && (RZ & (RZ - 1)) == 0, "ring sizes are powers of two");
+    static_assert(SHELL == VOL - TX * TY * TZ, "shell enumeration");
+    static_assert(TOP == TX * TY * TZ - (TX - 1) * (TY - 1) * (TZ - 1), "top-face enumeration");
+    static constexpr size_t smem_bytes() { return sizeof(float) * 7 * (size_t)VOL; }
+};
 
 // Shared-memory slot of ring position (sx, sy, sz).  Rows of 32 x-slots are
 // rotated by sy, so a warp reading one row, or reading one x-slot across the
 // y-slots, touches distinct banks; the rotation is a per-thread constant.
+template <class R>
 __device__ __forceinline__ int slot(int sx, int sy, int sz)
 {
-    return ((sz * RY + sy) << 5) | ((sx + sy) & 31);
+    return ((sz * R::RY + sy) << 5) | ((sx + sy) & 31);
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -98,12 +106,13 @@ __device__ __forceinline__ float ld_cg(const float *p)
 
 struct Interval { int s, e; };
 
+template <class R>
 __device__ __forceinline__ Interval tile_interval(const SysLaunch &P, int I, int J, int K)
 {
-    const int ax = I * TX, ay = J * TY, az = K * TZ;
+    const int ax = I * R::TX, ay = J * R::TY, az = K * R::TZ;
     Interval r;
     r.s = max(0, max(ax - P.nx + 1, max(ay - P.ny + 1, az - P.nz + 1)));
-    r.e = min(P.T - 1, min(ax + TX - 1, min(ay + TY - 1, az + TZ - 1)));
+    r.e = min(P.T - 1, min(ax + R::TX - 1, min(ay + R::TY - 1, az + R::TZ - 1)));
     return r;
 }
 
@@ -186,61 +195,65 @@ __device__ __forceinline__ long long gidx(const SysLaunch &P, int x, int y, int 
 //   cat 0 (z face): ring sx = a, sy = b
 //   cat 1 (y face, z not extra): ring sx = a, z offset b in [0, RZ-1)
 //   cat 2 (x face only): y offset a, z offset b in [0, RY-1) x [0, RZ-1)
+template <class R>
 __device__ __forceinline__ int shell_code(int f)
 {
-    if (f >= SHELL) return -1;
-    if (f < SHELL_Z) return 0 | ((f & 31) << 8) | ((f >> 5) << 16);
-    if (f < SHELL_Z + SHELL_Y) {
-        const int g = f - SHELL_Z;
+    if (f >= R::SHELL) return -1;
+    if (f < R::SHELL_Z) return 0 | ((f & 31) << 8) | ((f >> 5) << 16);
+    if (f < R::SHELL_Z + R::SHELL_Y) {
+        const int g = f - R::SHELL_Z;
         return 1 | ((g & 31) << 8) | ((g >> 5) << 16);
     }
-    const int g = f - SHELL_Z - SHELL_Y;
-    return 2 | ((g % (RY - 1)) << 8) | ((g / (RY - 1)) << 16);
+    const int g = f - R::SHELL_Z - R::SHELL_Y;
+    return 2 | ((g % (R::RY - 1)) << 8) | ((g / (R::RY - 1)) << 16);
 }
 
 // Ring slot and physical cell of a shell entry for the E window of step t,
 // whose lower corner is b - 1 and whose extra ring slot is e = (b-1) mod R.
+template <class R>
 __device__ __forceinline__ void shell_cell(int code, int bx, int by, int bz, int &o, int &px, int &py,
                                            int &pz)
 {
     const int cat = code & 0xff, a = (code >> 8) & 0xff, b = code >> 16;
-    const int ex = (bx - 1) & 31, ey = (by - 1) & (RY - 1), ez = (bz - 1) & (RZ - 1);
+    const int ex = (bx - 1) & 31, ey = (by - 1) & (R::RY - 1), ez = (bz - 1) & (R::RZ - 1);
     int sx, sy, sz;
     if (cat == 0) {
         sx = a; sy = b; sz = ez;
-        px = bx - 1 + ((a - bx + 1) & 31); py = by - 1 + ((b - by + 1) & (RY - 1)); pz = bz - 1;
+        px = bx - 1 + ((a - bx + 1) & 31); py = by - 1 + ((b - by + 1) & (R::RY - 1)); pz = bz - 1;
     } else if (cat == 1) {
-        sx = a; sy = ey; sz = (ez + 1 + b) & (RZ - 1);
+        sx = a; sy = ey; sz = (ez + 1 + b) & (R::RZ - 1);
         px = bx - 1 + ((a - bx + 1) & 31); py = by - 1; pz = bz + b;
     } else {
-        sx = ex; sy = (ey + 1 + a) & (RY - 1); sz = (ez + 1 + b) & (RZ - 1);
+        sx = ex; sy = (ey + 1 + a) & (R::RY - 1); sz = (ez + 1 + b) & (R::RZ - 1);
         px = bx - 1; py = by + a; pz = bz + b;
     }
-    o = slot(sx, sy, sz);
+    o = slot<R>(sx, sy, sz);
 }
 
 // Top-face entry f in [0, TOP): box offsets packed dx | dy << 8 | dz << 16.
+template <class R>
 __device__ __forceinline__ int top_code(int f)
 {
-    if (f >= TOP) return -1;
+    if (f >= R::TOP) return -1;
     int dx, dy, dz;
-    if (f < TOP_Z) {
-        dx = f % TX; dy = f / TX; dz = TZ - 1;
-    } else if (f < TOP_Z + TOP_Y) {
-        const int g = f - TOP_Z;
-        dx = g % TX; dz = g / TX; dy = TY - 1;
+    if (f < R::TOP_Z) {
+        dx = f % R::TX; dy = f / R::TX; dz = R::TZ - 1;
+    } else if (f < R::TOP_Z + R::TOP_Y) {
+        const int g = f - R::TOP_Z;
+        dx = g % R::TX; dz = g / R::TX; dy = R::TY - 1;
     } else {
-        const int g = f - TOP_Z - TOP_Y;
-        dx = TX - 1; dy = g % (TY - 1); dz = g / (TY - 1);
+        const int g = f - R::TOP_Z - R::TOP_Y;
+        dx = R::TX - 1; dy = g % (R::TY - 1); dz = g / (R::TY - 1);
     }
     return dx | (dy << 8) | (dz << 16);
 }
 
-constexpr int TOP_PT = (TOP + NTHREADS - 1) / NTHREADS;
-constexpr int ZS = RY * 32;  // floats between consecutive z rows of the ring
-
-__global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P)
+template <class R>
+__global__ void __launch_bounds__(R::NTHREADS, R::MINB) systolic_kernel(const SysLaunch P)
 {
+    constexpr int RY = R::RY, RZ = R::RZ, TX = R::TX, TY = R::TY, TZ = R::TZ;
+    constexpr int VOL = R::VOL, NTHREADS = R::NTHREADS, SHELL_PT = R::SHELL_PT, TOP_PT = R::TOP_PT;
+    constexpr int ZS = R::ZS;
     extern __shared__ float smem[];
     float *const sEx = smem, *const sEy = smem + VOL, *const sEz = smem + 2 * VOL;
     float *const sHx = smem + 3 * VOL, *const sHy = smem + 4 * VOL, *const sHz = smem + 5 * VOL;
@@ -263,9 +276,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
     const int o_ym = (sym << 5) | ((sx + sym) & 31);
     int sh_code[SHELL_PT], tp_code[TOP_PT];
 #pragma unroll
-    for (int q = 0; q < SHELL_PT; ++q) sh_code[q] = shell_code(tid + q * NTHREADS);
+    for (int q = 0; q < SHELL_PT; ++q) sh_code[q] = shell_code<R>(tid + q * NTHREADS);
 #pragma unroll
-    for (int q = 0; q < TOP_PT; ++q) tp_code[q] = top_code(tid + q * NTHREADS);
+    for (int q = 0; q < TOP_PT; ++q) tp_code[q] = top_code<R>(tid + q * NTHREADS);
 
     for (;;) {
         if (tid == 0) {
@@ -281,7 +294,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
         const int tile = P.tiles[ticket];
         const int I = tile % P.gx, J = (tile / P.gx) % P.gy, K = tile / (P.gx * P.gy);
         const int Ax = I * TX, Ay = J * TY, Az = K * TZ;
-        const Interval iv = tile_interval(P, I, J, K);
+        const Interval iv = tile_interval<R>(P, I, J, K);
         Upwind U;
         {
             const int nb[3][3] = {{I - 1, J, K}, {I, J - 1, K}, {I, J, K - 1}};
@@ -290,7 +303,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
                 if (nb[a][0] < 0 || nb[a][1] < 0 || nb[a][2] < 0) {
                     U.id[a] = -1; U.s[a] = 1; U.e[a] = -1;
                 } else {
-                    const Interval u = tile_interval(P, nb[a][0], nb[a][1], nb[a][2]);
+                    const Interval u = tile_interval<R>(P, nb[a][0], nb[a][1], nb[a][2]);
                     U.id[a] = nb[a][0] + P.gx * (nb[a][1] + P.gy * nb[a][2]);
                     U.s[a] = u.s; U.e[a] = u.e;
                 }
@@ -351,7 +364,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
                 sho[q] = -1;
                 if (sh_code[q] >= 0) {
                     int px, py, pz;
-                    shell_cell(sh_code[q], bx, by, bz, sho[q], px, py, pz);
+                    shell_cell<R>(sh_code[q], bx, by, bz, sho[q], px, py, pz);
                     if (in_dom(P, px, py, pz)) {
                         const long long g = gidx(P, px, py, pz);
 #pragma unroll
@@ -440,7 +453,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
                             const SrcDesc &s = P.src.s[q];
                             if (step < s.n_amp && s.i >= bx && s.i < bx + TX && s.j >= by &&
                                 s.j < by + TY && s.k >= bz && s.k < bz + TZ) {
-                                const int o = slot(s.i & 31, s.j & (RY - 1), s.k & (RZ - 1));
+                                const int o = slot<R>(s.i & 31, s.j & (RY - 1), s.k & (RZ - 1));
                                 sF[s.comp][o] = add_source(sF[s.comp][o], s.amp[step]);
                             }
                         }
@@ -472,7 +485,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
                         const int qx = bx + (code & 0xff), qy = by + ((code >> 8) & 0xff),
                                   qz = bz + (code >> 16);
                         if (in_dom(P, qx, qy, qz)) {
-                            const int o = slot(qx & 31, qy & (RY - 1), qz & (RZ - 1));
+                            const int o = slot<R>(qx & 31, qy & (RY - 1), qz & (RZ - 1));
                             const long long g = gidx(P, qx, qy, qz);
 #pragma unroll
                             for (int c = 0; c < 6; ++c) P.f[c][g] = sF[c][o];
@@ -492,27 +505,41 @@ __global__ void __launch_bounds__(NTHREADS, 1) systolic_kernel(const SysLaunch P
     }
 }
 
+using RingA = Ring<16, 16, 1>;  // 31 x 15 x 15 updated, 32 x 16 x 16 stored, 1 CTA per SM
+using RingB = Ring<8, 16, 2>;   // 31 x 7 x 15 updated, 32 x 8 x 16 stored, 2 CTAs per SM
+
+const SysShape kShapes[SYS_NSHAPES] = {{RingA::TX, RingA::TY, RingA::TZ}, {RingB::TX, RingB::TY, RingB::TZ}};
+
 } // namespace
 
-size_t systolic_smem_bytes() { return sizeof(float) * 7 * (size_t)VOL; }
+SysShape systolic_shape(int v) { return kShapes[v]; }
 
-cudaError_t systolic_configure()
+size_t systolic_smem_bytes(int v) { return v == 0 ? RingA::smem_bytes() : RingB::smem_bytes(); }
+
+cudaError_t systolic_configure(int v)
 {
-    return cudaFuncSetAttribute(systolic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)systolic_smem_bytes());
+    if (v == 0)
+        return cudaFuncSetAttribute(systolic_kernel<RingA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)RingA::smem_bytes());
+    return cudaFuncSetAttribute(systolic_kernel<RingB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RingB::smem_bytes());
 }
 
-cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st)
-{
-    systolic_kernel<<<grid, NTHREADS, systolic_smem_bytes(), st>>>(p);
-    return cudaGetLastError();
-}
-
-int systolic_max_ctas_per_sm()
+int systolic_max_ctas_per_sm(int v)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_kernel, NTHREADS,
-                                                      systolic_smem_bytes()) != cudaSuccess)
-        return 0;
-    return n;
+    cudaError_t e = v == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_kernel<RingA>,
+                                                                          RingA::NTHREADS, RingA::smem_bytes())
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_kernel<RingB>,
+                                                                          RingB::NTHREADS, RingB::smem_bytes());
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int v)
+{
+    if (v == 0)
+        systolic_kernel<RingA><<<grid, RingA::NTHREADS, RingA::smem_bytes(), st>>>(p);
+    else
+        systolic_kernel<RingB><<<grid, RingB::NTHREADS, RingB::smem_bytes(), st>>>(p);
+    return cudaGetLastError();
 }

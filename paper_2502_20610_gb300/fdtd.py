@@ -105,8 +105,12 @@ def _check(status, what):
         raise FdtdError(status, what)
 
 
+#: systolic tile shapes (updated cells x, y, z) the library is built with
+TILES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15)}
+
+
 def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
-                steps_per_launch=0, max_source_steps=0, boundary="pec"):
+                steps_per_launch=0, max_source_steps=0, boundary="pec", tile=None):
     nz, ny, nx = (int(s) for s in shape_zyx)
     g = Grid(nx, ny, nz)
     c = Coeffs()
@@ -118,6 +122,10 @@ def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
     c.wait_timeout_s = float(timeout_s)
     c.steps_per_launch = int(steps_per_launch)
     c.max_source_steps = int(max_source_steps)
+    if tile is not None:
+        t = TILES[tile] if isinstance(tile, str) else tuple(tile)
+        for a in range(3):
+            c.tile[a] = int(t[a])
     b = Boundary()
     b.kind = BOUNDARY[boundary]
     return g, c, b
@@ -152,7 +160,7 @@ class Sim:
     """
 
     def __init__(self, shape_zyx, eps, dt, scheme="systolic", device=None, timeout_s=2.0,
-                 steps_per_launch=0, max_source_steps=0):
+                 steps_per_launch=0, max_source_steps=0, tile=None):
         import torch
         self._lib = load_library()
         self.shape = tuple(int(s) for s in shape_zyx)
@@ -160,7 +168,8 @@ class Sim:
         self.scheme = scheme
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         g, c, b = make_params(self.shape, dt, scheme=scheme, timeout_s=timeout_s,
-                              steps_per_launch=steps_per_launch, max_source_steps=max_source_steps)
+                              steps_per_launch=steps_per_launch, max_source_steps=max_source_steps,
+                              tile=tile)
         self._params = (g, c, b)
         n = ctypes.c_size_t(0)
         _check(self._lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c), ctypes.byref(b),

@@ -53,11 +53,12 @@ def test_config1_gaussian_pulse_vs_oracle(cuda_device):
     ((1, 1, 1), 4),
     ((40, 1, 1), 9),
 ])
-def test_systolic_bitexact_naive_random_fields(cuda_device, shape, steps):
+@pytest.mark.parametrize("tile", sorted(fdtd.TILES))
+def test_systolic_bitexact_naive_random_fields(cuda_device, shape, steps, tile):
     eps = wl.random_eps(shape, 2)
     f0 = wl.random_fields(shape, 2, zero_pec_walls=False)  # static wall values too
     a, _ = run_gpu(shape, eps, f0, steps, "naive")
-    b, _ = run_gpu(shape, eps, f0, steps, "systolic")
+    b, _ = run_gpu(shape, eps, f0, steps, "systolic", tile=tile)
     assert bits_equal(a, b)
     ref = oracle_run(shape, eps, f0, steps, quantize=True)
     err = rel_l2_per_field(b.numpy(), ref)
@@ -75,7 +76,8 @@ def test_multi_launch_and_split_steps(cuda_device):
     assert bits_equal(a, b)
 
 
-def test_schedule_perturbations_stay_bitexact(cuda_device):
+@pytest.mark.parametrize("tile", sorted(fdtd.TILES))
+def test_schedule_perturbations_stay_bitexact(cuda_device, tile):
     """Other valid hand-out orders and injected per-tile delays must not
     change a single bit (race detection by result comparison)."""
     shape = (30, 45, 70)
@@ -84,7 +86,7 @@ def test_schedule_perturbations_stay_bitexact(cuda_device):
     ref, _ = run_gpu(shape, eps, f0, 40, "naive")
     for kind, ticket, p1, p2 in [(fdtd.DEBUG_ORDER, 7, 1, 0), (fdtd.DEBUG_ORDER, 0, 2, 0),
                                  (fdtd.DEBUG_DELAY, 1, 3, 20000), (fdtd.DEBUG_DELAY, 0, 2, 5000)]:
-        sim = fdtd.Sim(shape, eps, DT, scheme="systolic")
+        sim = fdtd.Sim(shape, eps, DT, scheme="systolic", tile=tile)
         sim.write_fields(torch.as_tensor(f0).cuda())
         sim.debug_set(kind, ticket, p1, p2)
         sim.step(40)

@@ -16,26 +16,27 @@ import numpy as np
 import pytest
 
 TX, TY, TZ = 31, 15, 15
+SHAPES = [(31, 15, 15), (31, 7, 15)]  # the tile shapes the library is built with
 
 
-def interval(I, J, K, N, T):
-    A = (I * TX, J * TY, K * TZ)
+def interval(I, J, K, N, T, n=(TX, TY, TZ)):
+    A = (I * n[0], J * n[1], K * n[2])
     s = max(0, A[0] - N[0] + 1, A[1] - N[1] + 1, A[2] - N[2] + 1)
-    e = min(T - 1, A[0] + TX - 1, A[1] + TY - 1, A[2] + TZ - 1)
+    e = min(T - 1, A[0] + n[0] - 1, A[1] + n[1] - 1, A[2] + n[2] - 1)
     return s, e
 
 
-def tile_order(N, T_max, order=0, seed=0):
+def tile_order(N, T_max, order=0, seed=0, n=(TX, TY, TZ)):
     """Same rule as the library: keep start <= end+1, sort by (start, I+J+K)."""
-    gx = -(-(N[0] + T_max - 1) // TX)
-    gy = -(-(N[1] + T_max - 1) // TY)
-    gz = -(-(N[2] + T_max - 1) // TZ)
+    gx = -(-(N[0] + T_max - 1) // n[0])
+    gy = -(-(N[1] + T_max - 1) // n[1])
+    gz = -(-(N[2] + T_max - 1) // n[2])
     rng = random.Random(seed)
     ent = []
     for K in range(gz):
         for J in range(gy):
             for I in range(gx):
-                s, e = interval(I, J, K, N, T_max)
+                s, e = interval(I, J, K, N, T_max, n)
                 if s > e + 1:
                     continue
                 key = (s, K, J, I) if order == 2 else (s, I + J + K, rng.random() if order == 1 else 0, I, J, K)
@@ -51,10 +52,10 @@ def box(lo, hi):
     return X.ravel(), Y.ravel(), Z.ravel()
 
 
-def run_model(N, T, n_cta=6, seed=0, order=0, T_max=None):
+def run_model(N, T, n_cta=6, seed=0, order=0, T_max=None, n=(TX, TY, TZ)):
     T_max = T_max or T
-    tiles, (gx, gy, gz) = tile_order(N, T_max, order, seed)
-    tiles = [t for t in tiles if interval(*t, N, T)[0] <= T]  # launch uses count_le[T]
+    tiles, (gx, gy, gz) = tile_order(N, T_max, order, seed, n)
+    tiles = [t for t in tiles if interval(*t, N, T, n)[0] <= T]  # launch uses count_le[T]
     rng = random.Random(seed)
     lvl = np.full((N[2], N[1], N[0]), -1, dtype=np.int64)
     count = np.zeros((T,) + lvl.shape, dtype=np.int32)
@@ -78,7 +79,7 @@ def run_model(N, T, n_cta=6, seed=0, order=0, T_max=None):
         for u in ((I - 1, J, K), (I, J - 1, K), (I, J, K - 1)):
             if min(u) < 0:
                 continue
-            s, e = interval(*u, N, T)
+            s, e = interval(*u, N, T, n)
             if s > e + 1 or L < s - 1 or L > e:
                 continue
             if progress.get(u, -10**9) < L + 1:
@@ -87,9 +88,8 @@ def run_model(N, T, n_cta=6, seed=0, order=0, T_max=None):
 
     def actions(tile):
         I, J, K = tile
-        A = (I * TX, J * TY, K * TZ)
-        n = (TX, TY, TZ)
-        s, e = interval(I, J, K, N, T)
+        A = (I * n[0], J * n[1], K * n[2])
+        s, e = interval(I, J, K, N, T, n)
         if s > 0:
             yield ("wait", s - 1)
         if s > e:
@@ -163,8 +163,9 @@ CASES = [
 
 @pytest.mark.parametrize("N,T", CASES)
 @pytest.mark.parametrize("order", [0, 1, 2])
-def test_schedule_levels_and_coverage(N, T, order):
-    errors, count, lvl = run_model(N, T, n_cta=5, seed=1 + order, order=order)
+@pytest.mark.parametrize("n", SHAPES)
+def test_schedule_levels_and_coverage(N, T, order, n):
+    errors, count, lvl = run_model(N, T, n_cta=5, seed=1 + order, order=order, n=n)
     assert not errors, errors[:5]
     assert np.all(count == 1), "every (cell, step) must be updated exactly once"
     assert np.all(lvl == T - 1), "after the launch global memory holds one uniform time level"
