@@ -169,6 +169,36 @@ void fdtd_destroy(fdtd_handle h);
 enum { FDTD_DEBUG_NONE = 0, FDTD_DEBUG_SKIP_PUBLISH = 1, FDTD_DEBUG_DELAY = 2, FDTD_DEBUG_ORDER = 3 };
 fdtd_status fdtd_debug_set(fdtd_handle h, int32_t kind, int64_t ticket, int64_t param, int64_t param2);
 
+/* Systolic step that allocates nothing (the paper has no counterpart; this
+ * is a library convenience).  Some callers cannot call cudaMalloc: a host
+ * application whose device memory is entirely owned by its own pool, or a
+ * plug-in that may not allocate device memory after start-up (cudaMalloc can
+ * also synchronise the device, which such callers must avoid).  They keep
+ * their own buffers and call this instead of fdtd_create/fdtd_step:
+ *   grid      nx, ny, nz >= 1;
+ *   d_fields  device, 6*nx*ny*nz floats, component-major Ex..Hz, x fastest,
+ *             state (E^n, H^{n-1/2}) in, (E^{n+n_steps}, H^{...-1/2}) out;
+ *   d_coef    device, nx*ny*nz floats, the E coefficient fl32(dt/eps) per cell;
+ *   dt        the time step used for H (must match d_coef);
+ *   stream    cudaStream_t the work is ordered on.
+ * PEC walls, no sources, tile 31x15x15; results are bit-identical to
+ * fdtd_step with FDTD_SCHEME_SYSTOLIC on the same state.
+ * Scratch: one file-scope device array of FDTD_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  Grids whose
+ * tile schedule does not fit it even one step per launch are rejected with
+ * FDTD_ERR_UNSUPPORTED (the message names the sizes); cubic grids up to
+ * about 1900^3 cells fit.
+ * The first call on a device looks up the array's device address and sets the
+ * kernel's shared-memory limit; make that first call before any stream
+ * capture.  Every call shares the array and clears it first, so calls that
+ * overlap on the GPU (two streams, two threads) race: serialise them.
+ * The call is synchronous: it returns after the steps finish, with
+ * FDTD_ERR_TIMEOUT if a device wait ran out, FDTD_ERR_CUDA on a CUDA error,
+ * FDTD_ERR_INVALID_ARG for null pointers, n_steps < 0 or dt <= 0. */
+#define FDTD_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *d_fields, const float *d_coef,
+                                       double dt, int64_t n_steps, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -164,6 +164,28 @@ void build_tiles(const fdtd_grid &g, const Layout &L, int order, unsigned seed,
 
 } // namespace
 
+// Tile hand-out order of the systolic scheme for one launch of up to T
+// steps with tile shape `variant` (same rule as a handle's schedule), for
+// callers that manage their own scratch.
+void systolic_tile_order(const fdtd_grid &g, int variant, int T, std::vector<int> &tiles,
+                         std::vector<long long> &count_le, int &gx, int &gy, int &gz)
+{
+    fdtd_coeffs c;
+    std::memset(&c, 0, sizeof(c));
+    c.scheme = FDTD_SCHEME_SYSTOLIC;
+    c.steps_per_launch = T;
+    const SysShape sh = systolic_shape(variant);
+    c.tile[0] = sh.tx;
+    c.tile[1] = sh.ty;
+    c.tile[2] = sh.tz;
+    Layout L;
+    make_layout(g, c, L);
+    build_tiles(g, L, 0, 0u, tiles, count_le);
+    gx = L.gx;
+    gy = L.gy;
+    gz = L.gz;
+}
+
 struct fdtd_sim {
     fdtd_grid g;
     fdtd_coeffs c;

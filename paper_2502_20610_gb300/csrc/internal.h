@@ -3,6 +3,9 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <vector>
+
+#include "fdtd.h"
 
 #define FDTD_MAX_SOURCES 16
 
@@ -61,3 +64,7 @@ size_t systolic_smem_bytes(int variant);
 cudaError_t systolic_configure(int variant);
 int systolic_max_ctas_per_sm(int variant);
 cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant);
+
+// Tile order for one systolic launch of up to T steps (fdtd_api.cu).
+void systolic_tile_order(const fdtd_grid &g, int variant, int T, std::vector<int> &tiles,
+                         std::vector<long long> &count_le, int &gx, int &gy, int &gz);

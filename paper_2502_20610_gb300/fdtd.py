@@ -24,7 +24,7 @@ DEBUG_NONE, DEBUG_SKIP_PUBLISH, DEBUG_DELAY, DEBUG_ORDER = range(4)
 EXPORTS = ("fdtd_workspace_size", "fdtd_create", "fdtd_add_source", "fdtd_write_fields",
            "fdtd_step", "fdtd_read_fields", "fdtd_sync", "fdtd_current_step",
            "fdtd_set_current_step", "fdtd_launch_count", "fdtd_status_string", "fdtd_destroy",
-           "fdtd_debug_set")
+           "fdtd_debug_set", "fdtd_systolic_step_noalloc")
 
 
 class Grid(ctypes.Structure):
@@ -89,6 +89,8 @@ def load_library(path=LIB_PATH):
     lib.fdtd_destroy.argtypes = [P]
     lib.fdtd_debug_set.restype = st
     lib.fdtd_debug_set.argtypes = [P, I32, I64, I64, I64]
+    lib.fdtd_systolic_step_noalloc.restype = st
+    lib.fdtd_systolic_step_noalloc.argtypes = [P, P, P, ctypes.c_double, I64, P]
     _lib = lib
     return lib
 
