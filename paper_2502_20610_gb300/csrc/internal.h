@@ -38,8 +38,11 @@ cudaError_t launch_naive_e(float *const f[6], const float *ce, int nx, int ny, i
 // 32 x 16 x 16 stored tile (one CTA per SM); shape 1 is 31 x 7 x 15 (two CTAs
 // per SM, so one hides the other's waits and barriers).
 struct SysShape { int tx, ty, tz; };
-constexpr int SYS_NSHAPES = 2;
+constexpr int SYS_NSHAPES = 3;  // 2: register-resident kernel, 31 x 15 x 12 (systolic_reg.cu)
 SysShape systolic_shape(int variant);
+SysShape systolic_reg_shape();
+cudaError_t systolic_reg_configure();
+int systolic_reg_max_ctas_per_sm();
 
 struct SysLaunch {
     float *f[6];
@@ -64,6 +67,7 @@ size_t systolic_smem_bytes(int variant);
 cudaError_t systolic_configure(int variant);
 int systolic_max_ctas_per_sm(int variant);
 cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant);
+cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st);
 
 // Tile order for one systolic launch of up to T steps (fdtd_api.cu).
 void systolic_tile_order(const fdtd_grid &g, int variant, int T, std::vector<int> &tiles,

@@ -31,9 +31,12 @@
 // Every arithmetic step is yee_cell.cuh, so the result equals the naive
 // schedule bit for bit.
 #include "internal.h"
+#include "sys_common.cuh"
 #include "yee_cell.cuh"
 
 namespace {
+
+using namespace sysc;
 
 // Ring geometry: RX x RY x RZ shared-memory slots per tile, (RX-1) x
 // (RY-1) x (RZ-1) cells updated per step, one thread per (x,y) ring column.
@@ -67,127 +70,6 @@ template <class R>
 __device__ __forceinline__ int slot(int sx, int sy, int sz)
 {
     return ((sz * R::RY + sy) << 5) | ((sx + sy) & 31);
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ int ld_volatile(const int *p)
-{
-    int v;
-    asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Loads of data produced by other CTAs during this launch go to L2 (.cg),
-// never to a possibly stale L1 line.
-__device__ __forceinline__ float ld_cg(const float *p)
-{
-    float v;
-    asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
-
-struct Interval { int s, e; };
-
-template <class R>
-__device__ __forceinline__ Interval tile_interval(const SysLaunch &P, int I, int J, int K)
-{
-    const int ax = I * R::TX, ay = J * R::TY, az = K * R::TZ;
-    Interval r;
-    r.s = max(0, max(ax - P.nx + 1, max(ay - P.ny + 1, az - P.nz + 1)));
-    r.e = min(P.T - 1, min(ax + R::TX - 1, min(ay + R::TY - 1, az + R::TZ - 1)));
-    return r;
-}
-
-// Progress flags of the three upwind face neighbours of the current tile,
-// and the last value seen on each (so most steps need no poll at all).
-struct Upwind {
-    int id[3];       // linear tile id, -1 if none
-    int s[3], e[3];  // their active intervals in this launch
-};
-
-// Wait until every -x, -y, -z neighbour that holds state at level L has
-// completed it (progress >= epoch + L + 1).  A neighbour u is waited on if
-// start(u)-1 <= L <= end(u) and start(u) <= end(u)+1: outside that range its
-// cells at level L lie outside the domain.  A neighbour that enters the
-// domain at L+1 publishes epoch+start(u) after its own initial wait, which
-// carries the guarantee of the tiles behind it.  Lanes 0..2 of warp 0 each
-// watch one neighbour; returns false (in every lane) if the launch aborts.
-__device__ bool wait_level(const SysLaunch &P, const Upwind &U, unsigned *seen, int L, int ticket)
-{
-    const int lane = threadIdx.x & 31;
-    bool ok = true;
-    if (lane < 3) {
-        const int a = lane;
-        // select this lane's neighbour without a dynamically indexed array
-        const int id = a == 0 ? U.id[0] : (a == 1 ? U.id[1] : U.id[2]);
-        const int us = a == 0 ? U.s[0] : (a == 1 ? U.s[1] : U.s[2]);
-        const int ue = a == 0 ? U.e[0] : (a == 1 ? U.e[1] : U.e[2]);
-        const unsigned target = P.epoch + (unsigned)L + 1u;
-        if (id >= 0 && us <= ue + 1 && L >= us - 1 && L <= ue && seen[a] < target) {
-            const unsigned *flag = P.progress + id;
-            unsigned long long t0 = 0;
-            for (int it = 0;; ++it) {
-                const unsigned v = ld_acquire(flag);
-                if (v >= target) {
-                    seen[a] = v;
-                    break;
-                }
-                if (ld_volatile(P.ctrl + 1) != DEV_OK) {
-                    ok = false;
-                    break;
-                }
-                const unsigned long long now = globaltimer();
-                if (it == 0) {
-                    t0 = now;
-                } else if (now - t0 > (unsigned long long)P.timeout_ns) {
-                    if (atomicCAS(P.ctrl + 1, DEV_OK, DEV_ERR_TIMEOUT) == DEV_OK) {
-                        P.ctrl[2] = ticket;
-                        P.ctrl[3] = (int)target;
-                    }
-                    ok = false;
-                    break;
-                }
-                __nanosleep(it < 64 ? 32 : 256);
-            }
-        }
-    }
-    return __all_sync(0xffffffffu, ok);
-}
-
-__device__ __forceinline__ void publish(const SysLaunch &P, int tile, int ticket, unsigned value)
-{
-    if (P.dbg_kind == 1 /* skip publish */ && ticket == P.dbg_ticket) return;
-    if (P.dbg_kind == 2 /* delay */ && P.dbg_param > 0 && (ticket % P.dbg_param) == P.dbg_ticket)
-        __nanosleep((unsigned)P.dbg_param2);
-    st_release(P.progress + tile, value);  // release: orders the CTA's stores before the flag
-}
-
-__device__ __forceinline__ bool in_dom(const SysLaunch &P, int x, int y, int z)
-{
-    return (unsigned)x < (unsigned)P.nx && (unsigned)y < (unsigned)P.ny && (unsigned)z < (unsigned)P.nz;
-}
-
-__device__ __forceinline__ long long gidx(const SysLaunch &P, int x, int y, int z)
-{
-    return x + (long long)P.nx * (y + (long long)P.ny * z);
 }
 
 // Shell entry f in [0, SHELL): face category and two coordinates inside the
@@ -294,7 +176,7 @@ __global__ void __launch_bounds__(R::NTHREADS, R::MINB) systolic_kernel(const Sy
         const int tile = P.tiles[ticket];
         const int I = tile % P.gx, J = (tile / P.gx) % P.gy, K = tile / (P.gx * P.gy);
         const int Ax = I * TX, Ay = J * TY, Az = K * TZ;
-        const Interval iv = tile_interval<R>(P, I, J, K);
+        const Interval iv = tile_interval<R::TX, R::TY, R::TZ>(P, I, J, K);
         Upwind U;
         {
             const int nb[3][3] = {{I - 1, J, K}, {I, J - 1, K}, {I, J, K - 1}};
@@ -303,7 +185,7 @@ __global__ void __launch_bounds__(R::NTHREADS, R::MINB) systolic_kernel(const Sy
                 if (nb[a][0] < 0 || nb[a][1] < 0 || nb[a][2] < 0) {
                     U.id[a] = -1; U.s[a] = 1; U.e[a] = -1;
                 } else {
-                    const Interval u = tile_interval<R>(P, nb[a][0], nb[a][1], nb[a][2]);
+                    const Interval u = tile_interval<R::TX, R::TY, R::TZ>(P, nb[a][0], nb[a][1], nb[a][2]);
                     U.id[a] = nb[a][0] + P.gx * (nb[a][1] + P.gy * nb[a][2]);
                     U.s[a] = u.s; U.e[a] = u.e;
                 }
@@ -508,16 +390,17 @@ __global__ void __launch_bounds__(R::NTHREADS, R::MINB) systolic_kernel(const Sy
 using RingA = Ring<16, 16, 1>;  // 31 x 15 x 15 updated, 32 x 16 x 16 stored, 1 CTA per SM
 using RingB = Ring<8, 16, 2>;   // 31 x 7 x 15 updated, 32 x 8 x 16 stored, 2 CTAs per SM
 
-const SysShape kShapes[SYS_NSHAPES] = {{RingA::TX, RingA::TY, RingA::TZ}, {RingB::TX, RingB::TY, RingB::TZ}};
+const SysShape kShapes[2] = {{RingA::TX, RingA::TY, RingA::TZ}, {RingB::TX, RingB::TY, RingB::TZ}};
 
 } // namespace
 
-SysShape systolic_shape(int v) { return kShapes[v]; }
+SysShape systolic_shape(int v) { return v == 2 ? systolic_reg_shape() : kShapes[v]; }
 
 size_t systolic_smem_bytes(int v) { return v == 0 ? RingA::smem_bytes() : RingB::smem_bytes(); }
 
 cudaError_t systolic_configure(int v)
 {
+    if (v == 2) return systolic_reg_configure();
     if (v == 0)
         return cudaFuncSetAttribute(systolic_kernel<RingA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)RingA::smem_bytes());
@@ -527,6 +410,7 @@ cudaError_t systolic_configure(int v)
 
 int systolic_max_ctas_per_sm(int v)
 {
+    if (v == 2) return systolic_reg_max_ctas_per_sm();
     int n = 0;
     cudaError_t e = v == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_kernel<RingA>,
                                                                           RingA::NTHREADS, RingA::smem_bytes())
@@ -537,6 +421,7 @@ int systolic_max_ctas_per_sm(int v)
 
 cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int v)
 {
+    if (v == 2) return launch_systolic_reg(p, grid, st);
     if (v == 0)
         systolic_kernel<RingA><<<grid, RingA::NTHREADS, RingA::smem_bytes(), st>>>(p);
     else

@@ -1,0 +1,480 @@
+// Systolic schedule, register-resident form (Sec. 3, Fig. 7; Sec. 4).
+//
+// Same method as systolic.cu: each CTA owns a tile, a box [A, A+n) of
+// skewed space sigma = p + t, scans it down the x-y-z-t diagonal, takes its
+// lower shell (level t) from the upwind tiles through global memory and
+// leaves its top faces there for the downwind ones, with per-tile progress
+// flags and no grid-wide synchronisation.  What differs is where the tile
+// lives: in registers instead of shared memory.
+//
+//   x: lane = physical x mod 32 (a ring, as in shared memory);
+//   y: warp = physical y mod 16 (a ring);
+//   z: register row r in [-1, NZ) = skewed z, sigma_z = A_z + r.
+//
+// Because rows are indexed by skewed z, the value a row needs from the
+// previous level sits one row below it in the same thread (sigma - 1 is the
+// same physical cell one step earlier): the diagonal scan is an implicit
+// register shift, H[r] <- f(H[r-1], E[r-1], E[r], ...), applied top-down in
+// place.  Row -1 holds the lower z shell.  x neighbours come by warp
+// shuffle, y neighbours through a small shared-memory exchange, so one cell
+// update costs 4 shared-memory loads/stores, 4 shuffles and 24 FP32
+// operations instead of ~27 shared-memory accesses.
+//
+// The slot that leaves the tile at the top in x (one lane per warp) and in y
+// (one warp) is refilled each step with the lower x / y shell: the y warp
+// loads its column rows itself (coalesced); the x columns are fetched by all
+// threads into a staging area that each x lane then reads with 16-byte
+// shared loads.  The top x face is written back the same way, one step late,
+// which is why a tile publishes level t at the second barrier of step t+1.
+//
+// Tile: 31 x 15 x NZ updated cells.  Every arithmetic step is yee_cell.cuh,
+// so the result equals the naive schedule bit for bit.
+#include "internal.h"
+#include "sys_common.cuh"
+#include "yee_cell.cuh"
+
+namespace {
+
+using namespace sysc;
+
+template <int NZ_>
+struct RegTile {
+    static constexpr int NZ = NZ_;        // updated z rows (registers 0..NZ-1)
+    static constexpr int NR = NZ_ + 1;    // plus the shell row -1
+    static constexpr int RY = 16, NT = 32 * RY;
+    static constexpr int TX = 31, TY = RY - 1, TZ = NZ_;
+    static constexpr int XSR = (NR + 3) / 4 * 4;  // staging rows per field, multiple of 4
+    static constexpr int NXS = TY * 7 * NR;       // x-shell staging entries (15 warps)
+    static constexpr int NXS_PT = (NXS + NT - 1) / NT;
+    static constexpr int NXO = TY * 6 * NZ;       // top x-face entries (15 warps)
+    static constexpr int NXO_PT = (NXO + NT - 1) / NT;
+    static_assert(NZ % 4 == 0, "top x face is staged with 16-byte stores");
+    // shared memory, in floats
+    static constexpr int XE_F = RY * NZ * 32;    // one exchanged component
+    static constexpr int XS_F = RY * 6 * XSR;
+    static constexpr int XO_F = RY * 6 * NZ;
+    static constexpr int CR = 16;                 // coefficient ring rows (>= NR, power of 2)
+    static constexpr int CE_F = RY * CR * 32;
+    static_assert(CR >= NR, "coefficient ring holds the whole column");
+    static constexpr size_t smem_bytes() { return sizeof(float) * (4 * (size_t)XE_F + XS_F + XO_F + CE_F); }
+};
+
+__device__ __forceinline__ float shfl_from(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+template <class R>
+__global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch P)
+{
+    constexpr int NZ = R::NZ, NR = R::NR, TX = R::TX, TY = R::TY, TZ = R::TZ, XSR = R::XSR;
+    extern __shared__ float4 smem4[];
+    float *const sm = reinterpret_cast<float *>(smem4);
+    float *const XEx = sm;                 // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
+    float *const XEz = XEx + R::XE_F;
+    float *const XHx = XEz + R::XE_F;      // [warp][row i-1][lane]: new H rows r = 0..NZ-1
+    float *const XHz = XHx + R::XE_F;
+    float *const XS = XHz + R::XE_F;       // [warp][field 0..5][XSR]: x shell column
+    float *const XO = XS + R::XS_F;        // [warp][field 0..5][NZ]: top x face
+    // dt/eps of each column, indexed by physical z mod CR: a cell's coefficient
+    // stays in place while the skewed register rows move past it
+    float *const CEs = XO + R::XO_F;       // [warp][physical z mod CR][lane]
+    __shared__ int s_ticket, s_abort;
+    __shared__ unsigned s_seen[3];
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const float ndt = P.neg_dt;
+    const long long sxy = (long long)P.nx * P.ny;
+    // field pointers are read from the kernel parameters where used (they stay
+    // in the constant bank instead of taking 14 registers)
+#define F0 P.f[0]
+#define F1 P.f[1]
+#define F2 P.f[2]
+#define F3 P.f[3]
+#define F4 P.f[4]
+#define F5 P.f[5]
+#define CE P.ce
+
+    // entries of the cooperative x-shell load / top x-face store handled by
+    // this thread (recomputed where used to keep registers for the column)
+#define XS_ENTRY(q, wi, f, i)                                                 \
+    const int e_##q = tid + (q) * R::NT;                                      \
+    const int wi = e_##q < R::NXS ? e_##q / (7 * NR) : -1;                    \
+    const int f = (e_##q % (7 * NR)) / NR;                                    \
+    const int i = e_##q % NR;
+#define XO_ENTRY(q, wi, f, r)                                                 \
+    const int o_##q = tid + (q) * R::NT;                                      \
+    const int wi = o_##q < R::NXO ? o_##q / (6 * NZ) : -1;                    \
+    const int f = (o_##q % (6 * NZ)) / NZ;                                    \
+    const int r = o_##q % NZ;
+
+    constexpr int CR = R::CR;
+    // the tile column of this thread: registers row i <-> r = i-1
+    float ex[NR], ey[NR], ez[NR], hx[NR], hy[NR], hz[NR];
+
+    for (;;) {
+        if (tid == 0) {
+            s_ticket = atomicAdd(P.ctrl, 1);
+            s_abort = ld_volatile(P.ctrl + 1) != DEV_OK;
+        }
+        if (tid < 3) s_seen[tid] = 0u;
+        __syncthreads();
+        const int ticket = s_ticket;
+        const bool stop = s_abort || ticket >= P.ntiles;
+        __syncthreads();
+        if (stop) break;
+        const int tile = P.tiles[ticket];
+        const int I = tile % P.gx, J = (tile / P.gx) % P.gy, K = tile / (P.gx * P.gy);
+        const int Ax = I * TX, Ay = J * TY, Az = K * TZ;
+        const Interval iv = tile_interval<TX, TY, TZ>(P, I, J, K);
+        Upwind U;
+        upwind_of<TX, TY, TZ>(P, I, J, K, U);
+
+        if (iv.s > 0) {
+            if (w == 0) {
+                const bool ok = wait_level(P, U, s_seen, iv.s - 1, ticket);
+                if (tid == 0) s_abort = !ok;
+            }
+            __syncthreads();
+            if (s_abort) break;
+        }
+        if (iv.s > iv.e) {  // enters the domain only after this launch: relay only
+            if (tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.s);
+            __syncthreads();
+            continue;
+        }
+
+        // initial load: level start-1, rows sigma_z = Az + r at physical Az + r - start + 1
+        {
+            const int bx = Ax - iv.s, by = Ay - iv.s;
+            const int px = bx + ((lane - bx) & 31), py = by + ((w - by) & (R::RY - 1));
+            const bool cin = (unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny;
+            const long long col = px + (long long)P.nx * py;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const int pz = Az + i - 1 - iv.s + 1;
+                float c = 0.f;
+                if (cin && (unsigned)pz < (unsigned)P.nz) {
+                    const long long g = col + sxy * pz;
+                    ex[i] = ld_cg(F0 + g); ey[i] = ld_cg(F1 + g); ez[i] = ld_cg(F2 + g);
+                    hx[i] = ld_cg(F3 + g); hy[i] = ld_cg(F4 + g); hz[i] = ld_cg(F5 + g);
+                    c = __ldg(CE + g);
+                } else {
+                    ex[i] = ey[i] = ez[i] = hx[i] = hy[i] = hz[i] = 0.f;
+                }
+                CEs[(w * CR + (pz & (CR - 1))) * 32 + lane] = c;
+            }
+        }
+        if (iv.s > 0 && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.s);
+
+        bool abort = false;
+        for (int t = iv.s; t <= iv.e; ++t) {
+            const int bx = Ax - t, by = Ay - t, bz = Az - t;  // box low corner at step t
+            const int dx = (lane - bx) & 31, dy = (w - by) & (R::RY - 1);
+            const int px = bx + dx, py = by + dy;
+            const bool xbox = dx < TX, ybox = dy < TY;
+            const bool colin = xbox && ybox && (unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny;
+            const int ey_w = (by - 1) & (R::RY - 1);  // warp holding the y shell this step
+            const long long col = px + (long long)P.nx * py;
+            // rows i with physical z = bz + i - 1 inside the domain
+            const int i_lo = max(1, 1 - bz), i_hi = min(NR, P.nz - bz + 1);
+
+            // A. publish E^t (old) rows for the warp below's H half-step
+#pragma unroll
+            for (int i = 0; i < NZ; ++i) {
+                XEx[(w * NZ + i) * 32 + lane] = ex[i];
+                XEz[(w * NZ + i) * 32 + lane] = ez[i];
+            }
+            if (w == 0) {
+                const bool ok = wait_level(P, U, s_seen, t, ticket);
+                if (tid == 0) s_abort = !ok;
+            }
+            __syncthreads();  // B1
+            if (s_abort) { abort = true; break; }
+
+            // B. global traffic of this step
+            if (t > iv.s) {  // top x face of step t-1, staged in XO
+                const int pbx = bx + 1, pby = by + 1, pbz = bz + 1;
+#pragma unroll
+                for (int q = 0; q < R::NXO_PT; ++q) {
+                    XO_ENTRY(q, wi, f, r)
+                    if (wi >= 0) {
+                        const int wv = (pby + wi) & (R::RY - 1);
+                        const int qx = pbx + TX - 1, qy = pby + wi, qz = pbz + r;
+                        if (in_dom(P, qx, qy, qz)) P.f[f][gidx(P, qx, qy, qz)] = XO[(wv * 6 + f) * NZ + r];
+                    }
+                }
+            }
+            // lower z shell (level t) for box columns
+            float nz_v[7];
+            {
+                const int pz = bz - 1;
+                if (colin && (unsigned)pz < (unsigned)P.nz) {
+                    const long long g = col + sxy * pz;
+                    nz_v[0] = ld_cg(F0 + g); nz_v[1] = ld_cg(F1 + g); nz_v[2] = ld_cg(F2 + g);
+                    nz_v[3] = ld_cg(F3 + g); nz_v[4] = ld_cg(F4 + g); nz_v[5] = ld_cg(F5 + g);
+                    nz_v[6] = __ldg(CE + g);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) nz_v[c] = 0.f;
+                }
+            }
+            // lower x shell columns of the 15 warps that are not the y shell
+            float xs_v[R::NXS_PT];
+#pragma unroll
+            for (int q = 0; q < R::NXS_PT; ++q) {
+                XS_ENTRY(q, wi, f, i)
+                xs_v[q] = 0.f;
+                if (wi >= 0) {
+                    const int qx = bx - 1, qy = by + wi, qz = bz + i - 1;
+                    if (in_dom(P, qx, qy, qz)) {
+                        const long long g = gidx(P, qx, qy, qz);
+                        xs_v[q] = f < 6 ? ld_cg(P.f[f] + g) : __ldg(CE + g);
+                    }
+                }
+            }
+            // the y shell warp refills its whole column set (level t)
+            if (w == ey_w) {
+                const int qx = (bx - 1) + ((lane - bx + 1) & 31), qy = by - 1;
+                const bool cin = (unsigned)qx < (unsigned)P.nx && (unsigned)qy < (unsigned)P.ny;
+                const long long c2 = qx + (long long)P.nx * qy;
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    const int pz = bz + i - 1;
+                    float c = 0.f;
+                    if (cin && (unsigned)pz < (unsigned)P.nz) {
+                        const long long g = c2 + sxy * pz;
+                        ex[i] = ld_cg(F0 + g); ey[i] = ld_cg(F1 + g); ez[i] = ld_cg(F2 + g);
+                        hx[i] = ld_cg(F3 + g); hy[i] = ld_cg(F4 + g); hz[i] = ld_cg(F5 + g);
+                        c = __ldg(CE + g);
+                    } else {
+                        ex[i] = ey[i] = ez[i] = hx[i] = hy[i] = hz[i] = 0.f;
+                    }
+                    CEs[(w * CR + (pz & (CR - 1))) * 32 + lane] = c;
+                }
+            }
+
+            // C. H half-step, top-down in place: H[i] <- H[i-1] - dt curl_f(E[i-1], E[i], ...)
+            if (w != ey_w) {
+                const int wn = (w + 1) & (R::RY - 1);
+                const int src = (lane + 1) & 31;
+#pragma unroll
+                for (int i = NR - 1; i >= 1; --i) {
+                    const float ez_xp = shfl_from(ez[i - 1], src);
+                    const float ey_xp = shfl_from(ey[i - 1], src);
+                    const float ez_yp = XEz[(wn * NZ + (i - 1)) * 32 + lane];
+                    const float ex_yp = XEx[(wn * NZ + (i - 1)) * 32 + lane];
+                    const float nhx = h_x(hx[i - 1], ez_yp, ez[i - 1], ey[i], ey[i - 1], ndt);
+                    const float nhy = h_y(hy[i - 1], ex[i], ex[i - 1], ez_xp, ez[i - 1], ndt);
+                    const float nhz = h_z(hz[i - 1], ey_xp, ey[i - 1], ex_yp, ex[i - 1], ndt);
+                    const bool upd = colin && i >= i_lo && i < i_hi;
+                    hx[i] = upd ? nhx : hx[i - 1];
+                    hy[i] = upd ? nhy : hy[i - 1];
+                    hz[i] = upd ? nhz : hz[i - 1];
+                }
+                // row -1 now takes the lower z shell's H (level t)
+                hx[0] = nz_v[3]; hy[0] = nz_v[4]; hz[0] = nz_v[5];
+            }
+
+            // D. publish new H rows for the warp above's E half-step; stage the x shell
+#pragma unroll
+            for (int i = 1; i < NR; ++i) {
+                XHx[(w * NZ + (i - 1)) * 32 + lane] = hx[i];
+                XHz[(w * NZ + (i - 1)) * 32 + lane] = hz[i];
+            }
+#pragma unroll
+            for (int q = 0; q < R::NXS_PT; ++q) {
+                XS_ENTRY(q, wi, f, i)
+                if (wi >= 0) {
+                    const int wv = (by + wi) & (R::RY - 1);
+                    if (f < 6)
+                        XS[(wv * 6 + f) * XSR + i] = xs_v[q];
+                    else
+                        CEs[(wv * CR + ((bz + i - 1) & (CR - 1))) * 32 + ((bx - 1) & 31)] = xs_v[q];
+                }
+            }
+            if (w != ey_w && xbox) CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = nz_v[6];
+            __syncthreads();  // B2
+            if (t > iv.s && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)t);  // level t-1 done
+
+            if (w != ey_w) {
+                // E. the lane leaving the tile in x takes the x shell's H
+                const float *xs = XS + w * 6 * XSR;
+                if (!xbox) {
+#pragma unroll
+                    for (int k = 0; k < XSR / 4; ++k) {
+                        const float4 a = *reinterpret_cast<const float4 *>(xs + 3 * XSR + 4 * k);
+                        const float4 b = *reinterpret_cast<const float4 *>(xs + 4 * XSR + 4 * k);
+                        const float4 c = *reinterpret_cast<const float4 *>(xs + 5 * XSR + 4 * k);
+                        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w},
+                                    cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (4 * k + u < NR) {
+                                hx[4 * k + u] = av[u]; hy[4 * k + u] = bv[u]; hz[4 * k + u] = cv[u];
+                            }
+                        }
+                    }
+                }
+                // F. E half-step, top-down in place: E[i] <- E[i-1] + ce curl_b(H[i], H[i-1], ...)
+                const int wm = (w - 1) & (R::RY - 1);
+                const int src = (lane - 1) & 31;
+                const bool ux = py > 0, uy = px > 0, uz = px > 0 && py > 0;
+#pragma unroll
+                for (int i = NR - 1; i >= 1; --i) {
+                    const float hz_xm = shfl_from(hz[i], src);
+                    const float hy_xm = shfl_from(hy[i], src);
+                    const float hx_ym = XHx[(wm * NZ + (i - 1)) * 32 + lane];
+                    const float hz_ym = XHz[(wm * NZ + (i - 1)) * 32 + lane];
+                    const float c = CEs[(w * CR + ((bz + i - 1) & (CR - 1))) * 32 + lane];
+                    const float nex = e_x(ex[i - 1], hz[i], hz_ym, hy[i], hy[i - 1], c);
+                    const float ney = e_y(ey[i - 1], hx[i], hx[i - 1], hz[i], hz_xm, c);
+                    const float nez = e_z(ez[i - 1], hy[i], hy_xm, hx[i], hx_ym, c);
+                    const bool in = colin && i >= i_lo && i < i_hi;
+                    const bool kz = bz + i - 1 > 0;
+                    ex[i] = (in && ux && kz) ? nex : ex[i - 1];
+                    ey[i] = (in && uy && kz) ? ney : ey[i - 1];
+                    ez[i] = (in && uz) ? nez : ez[i - 1];
+                }
+                // row -1 takes the lower z shell's E and coefficient (level t)
+                ex[0] = nz_v[0]; ey[0] = nz_v[1]; ez[0] = nz_v[2];
+                // the x lane takes the rest of its shell column
+                if (!xbox) {
+#pragma unroll
+                    for (int k = 0; k < XSR / 4; ++k) {
+                        const float4 a = *reinterpret_cast<const float4 *>(xs + 0 * XSR + 4 * k);
+                        const float4 b = *reinterpret_cast<const float4 *>(xs + 1 * XSR + 4 * k);
+                        const float4 c = *reinterpret_cast<const float4 *>(xs + 2 * XSR + 4 * k);
+                        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w},
+                                    cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (4 * k + u < NR) {
+                                ex[4 * k + u] = av[u]; ey[4 * k + u] = bv[u]; ez[4 * k + u] = cv[u];
+                            }
+                        }
+                    }
+                }
+            }
+
+            // point sources inside the box: the owning thread adds them
+            {
+                const long long step = P.step0 + t;
+                for (int q = 0; q < P.src.n; ++q) {
+                    const SrcDesc &s = P.src.s[q];
+                    if (step < s.n_amp && s.i >= bx && s.i < bx + TX && s.j >= by && s.j < by + TY &&
+                        s.k >= bz && s.k < bz + TZ && lane == (s.i & 31) && w == (s.j & (R::RY - 1))) {
+                        const float a = s.amp[step];
+                        const int ri = s.k - bz + 1;
+#pragma unroll
+                        for (int i = 1; i < NR; ++i) {
+                            if (i == ri) {
+                                if (s.comp == 0) ex[i] = add_source(ex[i], a);
+                                else if (s.comp == 1) ey[i] = add_source(ey[i], a);
+                                else ez[i] = add_source(ez[i], a);
+                            }
+                        }
+                    }
+                }
+            }
+
+            // G. stores: the whole box on the launch's last step, else the top faces
+            if (t == P.T - 1) {
+                if (colin) {
+#pragma unroll
+                    for (int i = 1; i < NR; ++i) {
+                        if (i >= i_lo && i < i_hi) {
+                            const long long g = col + sxy * (bz + i - 1);
+                            F0[g] = ex[i]; F1[g] = ey[i]; F2[g] = ez[i];
+                            F3[g] = hx[i]; F4[g] = hy[i]; F5[g] = hz[i];
+                        }
+                    }
+                }
+            } else {
+                if (colin) {
+                    if (dy == TY - 1) {  // top y face: the whole column
+#pragma unroll
+                        for (int i = 1; i < NR; ++i) {
+                            if (i >= i_lo && i < i_hi) {
+                                const long long g = col + sxy * (bz + i - 1);
+                                F0[g] = ex[i]; F1[g] = ey[i]; F2[g] = ez[i];
+                                F3[g] = hx[i]; F4[g] = hy[i]; F5[g] = hz[i];
+                            }
+                        }
+                    } else if (NR - 1 >= i_lo && NR - 1 < i_hi) {  // top z face
+                        const long long g = col + sxy * (bz + NR - 2);
+                        F0[g] = ex[NR - 1]; F1[g] = ey[NR - 1]; F2[g] = ez[NR - 1];
+                        F3[g] = hx[NR - 1]; F4[g] = hy[NR - 1]; F5[g] = hz[NR - 1];
+                    }
+                }
+                if (ybox && dx == TX - 1) {  // top x face: staged, stored at B1 of the next step
+                    float *xo = XO + w * 6 * NZ;
+#pragma unroll
+                    for (int k = 0; k < NZ / 4; ++k) {
+                        *reinterpret_cast<float4 *>(xo + 0 * NZ + 4 * k) =
+                            make_float4(ex[4 * k + 1], ex[4 * k + 2], ex[4 * k + 3], ex[4 * k + 4]);
+                        *reinterpret_cast<float4 *>(xo + 1 * NZ + 4 * k) =
+                            make_float4(ey[4 * k + 1], ey[4 * k + 2], ey[4 * k + 3], ey[4 * k + 4]);
+                        *reinterpret_cast<float4 *>(xo + 2 * NZ + 4 * k) =
+                            make_float4(ez[4 * k + 1], ez[4 * k + 2], ez[4 * k + 3], ez[4 * k + 4]);
+                        *reinterpret_cast<float4 *>(xo + 3 * NZ + 4 * k) =
+                            make_float4(hx[4 * k + 1], hx[4 * k + 2], hx[4 * k + 3], hx[4 * k + 4]);
+                        *reinterpret_cast<float4 *>(xo + 4 * NZ + 4 * k) =
+                            make_float4(hy[4 * k + 1], hy[4 * k + 2], hy[4 * k + 3], hy[4 * k + 4]);
+                        *reinterpret_cast<float4 *>(xo + 5 * NZ + 4 * k) =
+                            make_float4(hz[4 * k + 1], hz[4 * k + 2], hz[4 * k + 3], hz[4 * k + 4]);
+                    }
+                }
+            }
+        }
+        if (abort) break;
+        // the last step's staged top x face, then its progress
+        __syncthreads();
+        if (iv.e < P.T - 1) {
+            const int pbx = Ax - iv.e, pby = Ay - iv.e, pbz = Az - iv.e;
+#pragma unroll
+            for (int q = 0; q < R::NXO_PT; ++q) {
+                XO_ENTRY(q, wi, f, r)
+                if (wi >= 0) {
+                    const int wv = (pby + wi) & (R::RY - 1);
+                    const int qx = pbx + TX - 1, qy = pby + wi, qz = pbz + r;
+                    if (in_dom(P, qx, qy, qz)) P.f[f][gidx(P, qx, qy, qz)] = XO[(wv * 6 + f) * NZ + r];
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.e + 1u);
+    }
+}
+
+#undef F0
+#undef F1
+#undef F2
+#undef F3
+#undef F4
+#undef F5
+#undef CE
+#undef XS_ENTRY
+#undef XO_ENTRY
+
+using RegA = RegTile<12>;
+
+} // namespace
+
+SysShape systolic_reg_shape() { return {RegA::TX, RegA::TY, RegA::TZ}; }
+
+cudaError_t systolic_reg_configure()
+{
+    return cudaFuncSetAttribute(systolic_reg_kernel<RegA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RegA::smem_bytes());
+}
+
+int systolic_reg_max_ctas_per_sm()
+{
+    int n = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_reg_kernel<RegA>, RegA::NT,
+                                                         RegA::smem_bytes()) == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st)
+{
+    systolic_reg_kernel<RegA><<<grid, RegA::NT, RegA::smem_bytes(), st>>>(p);
+    return cudaGetLastError();
+}

@@ -108,7 +108,7 @@ def _check(status, what):
 
 
 #: systolic tile shapes (updated cells x, y, z) the library is built with
-TILES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15)}
+TILES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15), "31x15x12": (31, 15, 12)}
 
 
 def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
