@@ -22,6 +22,7 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     size_t fields[6], ce, src, progress, tiles, ctrl, total;
+    int pitch;  // floats per x row in device memory (nx rounded up to 16 bytes)
     int variant, tx, ty, tz;  // systolic tile shape
     int gx, gy, gz;
     long long ntiles_max;
@@ -48,7 +49,10 @@ int pick_variant(const fdtd_coeffs &c)
 //   and (systolic) one progress flag per skewed tile plus the tile order.
 bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, Layout &L)
 {
-    const long long n = (long long)g.nx * g.ny * g.nz;
+    // rows padded to a 16-byte multiple, so every row starts 16-byte aligned
+    // (a requirement of bulk tensor copies); the padding cells are never read
+    L.pitch = (g.nx + 3) / 4 * 4;
+    const long long n = (long long)L.pitch * g.ny * g.nz;
     size_t off = 0;
     for (int k = 0; k < 6; ++k) {
         L.fields[k] = off;
@@ -220,6 +224,18 @@ fdtd_status cuda_status(cudaError_t e)
     return FDTD_ERR_CUDA;
 }
 
+// Copy ny*nz rows of nx floats between a dense array and a pitched one
+// (one flat copy when the pitch adds no padding).
+cudaError_t copy_rows(float *dst, size_t dpitch, const float *src, size_t spitch, const fdtd_grid &g,
+                      cudaStream_t st)
+{
+    const size_t rows = (size_t)g.ny * g.nz, w = sizeof(float) * g.nx;
+    if (dpitch == (size_t)g.nx && spitch == (size_t)g.nx)
+        return cudaMemcpyAsync(dst, src, w * rows, cudaMemcpyDefault, st);
+    return cudaMemcpy2DAsync(dst, sizeof(float) * dpitch, src, sizeof(float) * spitch, w, rows,
+                             cudaMemcpyDefault, st);
+}
+
 #define CK(x)                                                                  \
     do {                                                                       \
         cudaError_t e_ = (x);                                                  \
@@ -299,10 +315,14 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     // E coefficient: dt/eps in FP64, rounded to FP32 once per cell
     std::vector<float> ce((size_t)n);
     for (long long p = 0; p < n; ++p) ce[(size_t)p] = (float)(coeffs->dt / eps[p]);
-    cudaError_t e = cudaMemcpyAsync(h->ce, ce.data(), sizeof(float) * (size_t)n, cudaMemcpyHostToDevice,
-                                    h->stream);
+    const size_t padded = (size_t)L.pitch * grid->ny * grid->nz;
+    cudaError_t e = cudaMemsetAsync(h->ce, 0, sizeof(float) * padded, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(h->ce, sizeof(float) * L.pitch, ce.data(), sizeof(float) * grid->nx,
+                              sizeof(float) * grid->nx, (size_t)grid->ny * grid->nz, cudaMemcpyHostToDevice,
+                              h->stream);
     for (int k = 0; k < 6 && e == cudaSuccess; ++k)
-        e = cudaMemsetAsync(h->f[k], 0, sizeof(float) * (size_t)n, h->stream);
+        e = cudaMemsetAsync(h->f[k], 0, sizeof(float) * padded, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ctrl, 0, 64 * sizeof(int), h->stream);
     if (e == cudaSuccess && L.ntiles_max > 0)
         e = cudaMemsetAsync(h->progress, 0, sizeof(unsigned) * (size_t)L.ntiles_max, h->stream);
@@ -335,8 +355,9 @@ fdtd_status fdtd_add_source(fdtd_handle h, int32_t component, int32_t i, int32_t
     if (i < 0 || j < 0 || k < 0 || i >= h->g.nx || j >= h->g.ny || k >= h->g.nz) return FDTD_ERR_INVALID_ARG;
     if (n_steps > h->L.source_steps) return FDTD_ERR_INVALID_ARG;
     if (h->src.n >= FDTD_MAX_SOURCES) return FDTD_ERR_STATE;
-    const long long idx = i + (long long)h->g.nx * (j + (long long)h->g.ny * k);
-    const double c = h->c.dt / h->eps_host[(size_t)idx];
+    const long long dense = i + (long long)h->g.nx * (j + (long long)h->g.ny * k);
+    const long long idx = i + (long long)h->L.pitch * (j + (long long)h->g.ny * k);
+    const double c = h->c.dt / h->eps_host[(size_t)dense];
     std::vector<float> amp((size_t)std::max<int64_t>(n_steps, 1));
     for (int64_t n = 0; n < n_steps; ++n) amp[(size_t)n] = (float)(-c * J[n]);
     float *dst = h->src_tab + (size_t)h->src.n * (size_t)h->L.source_steps;
@@ -361,7 +382,7 @@ fdtd_status fdtd_write_fields(fdtd_handle h, const float *src)
     if (!h || !src) return FDTD_ERR_INVALID_ARG;
     const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
     for (int k = 0; k < 6; ++k)
-        CK(cudaMemcpyAsync(h->f[k], src + (size_t)k * n, sizeof(float) * n, cudaMemcpyDefault, h->stream));
+        CK(copy_rows(h->f[k], h->L.pitch, src + (size_t)k * n, h->g.nx, h->g, h->stream));
     CK(cudaMemsetAsync(h->ctrl + 1, 0, 3 * sizeof(int), h->stream));
     h->failed = false;
     return FDTD_OK;
@@ -374,8 +395,9 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
     if (h->c.scheme == FDTD_SCHEME_NAIVE) {
         const float ndt = -(float)h->c.dt;
         for (int64_t s = 0; s < n; ++s) {
-            CK(launch_naive_h(h->f, h->g.nx, h->g.ny, h->g.nz, ndt, h->stream));
-            CK(launch_naive_e(h->f, h->ce, h->g.nx, h->g.ny, h->g.nz, h->step, h->src, h->stream));
+            CK(launch_naive_h(h->f, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->stream));
+            CK(launch_naive_e(h->f, h->ce, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->step, h->src,
+                              h->stream));
             h->launches += 2;
             h->step += 1;
         }
@@ -394,6 +416,9 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         p.nx = h->g.nx;
         p.ny = h->g.ny;
         p.nz = h->g.nz;
+        p.pitch = h->L.pitch;
+        p.fbase = h->f[0];
+        p.fstride = (long long)(h->L.fields[1] - h->L.fields[0]) / (long long)sizeof(float);
         p.gx = h->L.gx;
         p.gy = h->L.gy;
         p.gz = h->L.gz;
@@ -444,7 +469,7 @@ fdtd_status fdtd_read_fields(fdtd_handle h, uint32_t component_mask, float *dst)
     size_t q = 0;
     for (int k = 0; k < 6; ++k) {
         if (!(component_mask & (1u << k))) continue;
-        CK(cudaMemcpyAsync(dst + q * n, h->f[k], sizeof(float) * n, cudaMemcpyDefault, h->stream));
+        CK(copy_rows(dst + q * n, h->g.nx, h->f[k], h->L.pitch, h->g, h->stream));
         ++q;
     }
     CK(cudaStreamSynchronize(h->stream));

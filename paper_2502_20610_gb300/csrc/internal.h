@@ -16,7 +16,7 @@ enum : int { DEV_OK = 0, DEV_ERR_TIMEOUT = 1 };
 // (i,j,k) receives amp[n] after the E half-step of absolute step n < n_amp.
 struct SrcDesc {
     int comp, i, j, k;
-    long long idx;
+    long long idx;           // i + pitch*(j + ny*k)
     long long n_amp;
     const float *amp;
 };
@@ -27,9 +27,10 @@ struct SrcSet {
 };
 
 // Naive scheme: one H launch and one E launch per step.
-cudaError_t launch_naive_h(float *const f[6], int nx, int ny, int nz, float neg_dt,
+// Arrays are nx*ny*nz cells with rows of `pitch` floats (pitch >= nx).
+cudaError_t launch_naive_h(float *const f[6], int nx, int ny, int nz, int pitch, float neg_dt,
                            cudaStream_t st);
-cudaError_t launch_naive_e(float *const f[6], const float *ce, int nx, int ny, int nz,
+cudaError_t launch_naive_e(float *const f[6], const float *ce, int nx, int ny, int nz, int pitch,
                            long long step, const SrcSet &src, cudaStream_t st);
 
 // Systolic scheme: the subdomain ("tile") geometry is a compile-time ring of
@@ -38,16 +39,19 @@ cudaError_t launch_naive_e(float *const f[6], const float *ce, int nx, int ny, i
 // 32 x 16 x 16 stored tile (one CTA per SM); shape 1 is 31 x 7 x 15 (two CTAs
 // per SM, so one hides the other's waits and barriers).
 struct SysShape { int tx, ty, tz; };
-constexpr int SYS_NSHAPES = 3;  // 2: register-resident kernel, 31 x 15 x 12 (systolic_reg.cu)
+constexpr int SYS_NSHAPES = 4;  // 2, 3: register-resident kernel, 31 x 15 x 12 / x 8 (systolic_reg.cu)
 SysShape systolic_shape(int variant);
-SysShape systolic_reg_shape();
-cudaError_t systolic_reg_configure();
-int systolic_reg_max_ctas_per_sm();
+SysShape systolic_reg_shape(int k);
+cudaError_t systolic_reg_configure(int k);
+int systolic_reg_max_ctas_per_sm(int k);
 
 struct SysLaunch {
     float *f[6];
     const float *ce;
     int nx, ny, nz;
+    int pitch;               // floats between consecutive x rows (>= nx)
+    float *fbase;            // f[c] == fbase + c*fstride for c in 0..5 and ce == fbase + 6*fstride,
+    long long fstride;       // when the arrays sit at a uniform stride (else fstride == 0)
     int gx, gy, gz;          // tile grid over skewed space sigma = p + t
     int T;                   // steps of this launch
     unsigned epoch;          // progress values of this launch are epoch + k
@@ -67,7 +71,7 @@ size_t systolic_smem_bytes(int variant);
 cudaError_t systolic_configure(int variant);
 int systolic_max_ctas_per_sm(int variant);
 cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant);
-cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st);
+cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k);
 
 // Tile order for one systolic launch of up to T steps (fdtd_api.cu).
 void systolic_tile_order(const fdtd_grid &g, int variant, int T, std::vector<int> &tiles,

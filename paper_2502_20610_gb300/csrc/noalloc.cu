@@ -124,6 +124,9 @@ extern "C" fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *
     p.nx = g.nx;
     p.ny = g.ny;
     p.nz = g.nz;
+    p.pitch = g.nx;  // the caller's dense arrays
+    p.fbase = d_fields;
+    p.fstride = 0;   // the coefficient is a separate buffer
     p.gx = gx;
     p.gy = gy;
     p.gz = gz;

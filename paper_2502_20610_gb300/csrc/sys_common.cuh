@@ -33,13 +33,9 @@ __device__ __forceinline__ unsigned long long globaltimer()
 }
 
 // Loads of data produced by other CTAs during this launch go to L2 (.cg),
-// never to a possibly stale L1 line.
-__device__ __forceinline__ float ld_cg(const float *p)
-{
-    float v;
-    asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
+// never to a possibly stale L1 line.  The intrinsic (not volatile asm) lets
+// the compiler batch independent loads; barriers still order them.
+__device__ __forceinline__ float ld_cg(const float *p) { return __ldcg(p); }
 
 struct Interval { int s, e; };
 
@@ -127,7 +123,7 @@ __device__ __forceinline__ bool in_dom(const SysLaunch &P, int x, int y, int z)
 
 __device__ __forceinline__ long long gidx(const SysLaunch &P, int x, int y, int z)
 {
-    return x + (long long)P.nx * (y + (long long)P.ny * z);
+    return x + (long long)P.pitch * (y + (long long)P.ny * z);
 }
 
 

@@ -267,19 +267,25 @@ __global__ void __launch_bounds__(R::NTHREADS, R::MINB) systolic_kernel(const Sy
             const int dz_lo = max(0, -bz), dz_hi = min(TZ, P.nz - bz);
             const int r0 = bz & (RZ - 1);
 
-            // 2. H half-step on the box
+            // 2. H half-step on the box.  The thread walks the 16 ring rows of its
+            //    column in fixed order (row r holds box offset dz = (r - r0) mod RZ,
+            //    dz = TZ being the trailing row), so every shared-memory address is
+            //    a per-thread base plus a constant.
             if (col) {
-                float exc = sEx[r0 * ZS + o_s], eyc = sEy[r0 * ZS + o_s];
+                float exc = sEx[o_s], eyc = sEy[o_s];
+                const float ex0 = exc, ey0 = eyc;
 #pragma unroll
-                for (int dz = 0; dz < TZ; ++dz) {
-                    const int rb = ((r0 + dz) & (RZ - 1)) * ZS;
-                    const int rn = ((r0 + dz + 1) & (RZ - 1)) * ZS;
-                    const float exn = sEx[rn + o_s], eyn = sEy[rn + o_s];
+                for (int r = 0; r < RZ; ++r) {
+                    const int rn = (r + 1) & (RZ - 1);
+                    const float exn = rn == 0 ? ex0 : sEx[rn * ZS + o_s];
+                    const float eyn = rn == 0 ? ey0 : sEy[rn * ZS + o_s];
+                    const int dz = (r - r0) & (RZ - 1);
                     if (dz >= dz_lo && dz < dz_hi) {
-                        const float ez = sEz[rb + o_s];
-                        sHx[rb + o_s] = h_x(sHx[rb + o_s], sEz[rb + o_yp], ez, eyn, eyc, ndt);
-                        sHy[rb + o_s] = h_y(sHy[rb + o_s], exn, exc, sEz[rb + o_xp], ez, ndt);
-                        sHz[rb + o_s] = h_z(sHz[rb + o_s], sEy[rb + o_xp], eyc, sEx[rb + o_yp], exc, ndt);
+                        const int o = r * ZS + o_s;
+                        const float ez = sEz[o];
+                        sHx[o] = h_x(sHx[o], sEz[r * ZS + o_yp], ez, eyn, eyc, ndt);
+                        sHy[o] = h_y(sHy[o], exn, exc, sEz[r * ZS + o_xp], ez, ndt);
+                        sHz[o] = h_z(sHz[o], sEy[r * ZS + o_xp], eyc, sEx[r * ZS + o_yp], exc, ndt);
                     }
                     exc = exn;
                     eyc = eyn;
@@ -298,21 +304,22 @@ __global__ void __launch_bounds__(R::NTHREADS, R::MINB) systolic_kernel(const Sy
             }
             __syncthreads();
 
-            // 4. E half-step on the box; PEC: tangential E on low planes fixed
+            // 4. E half-step on the box, same row order; PEC: tangential E on low
+            //    planes fixed
             if (col) {
-                const int rm = ((r0 - 1) & (RZ - 1)) * ZS;
-                float hxm = sHx[rm + o_s], hym = sHy[rm + o_s];
                 const bool ux = py > 0, uy = px > 0, uz = px > 0 && py > 0;
+                float hxm = sHx[(RZ - 1) * ZS + o_s], hym = sHy[(RZ - 1) * ZS + o_s];
 #pragma unroll
-                for (int dz = 0; dz < TZ; ++dz) {
-                    const int rb = ((r0 + dz) & (RZ - 1)) * ZS;
-                    const float hx = sHx[rb + o_s], hy = sHy[rb + o_s];
+                for (int r = 0; r < RZ; ++r) {
+                    const int o = r * ZS + o_s;
+                    const float hx = sHx[o], hy = sHy[o];
+                    const int dz = (r - r0) & (RZ - 1);
                     if (dz >= dz_lo && dz < dz_hi) {
-                        const float hz = sHz[rb + o_s], ce = sCE[rb + o_s];
+                        const float hz = sHz[o], ce = sCE[o];
                         const bool kz = bz + dz > 0;
-                        if (ux && kz) sEx[rb + o_s] = e_x(sEx[rb + o_s], hz, sHz[rb + o_ym], hy, hym, ce);
-                        if (uy && kz) sEy[rb + o_s] = e_y(sEy[rb + o_s], hx, hxm, hz, sHz[rb + o_xm], ce);
-                        if (uz) sEz[rb + o_s] = e_z(sEz[rb + o_s], hy, sHy[rb + o_xm], hx, sHx[rb + o_ym], ce);
+                        if (ux && kz) sEx[o] = e_x(sEx[o], hz, sHz[r * ZS + o_ym], hy, hym, ce);
+                        if (uy && kz) sEy[o] = e_y(sEy[o], hx, hxm, hz, sHz[r * ZS + o_xm], ce);
+                        if (uz) sEz[o] = e_z(sEz[o], hy, sHy[r * ZS + o_xm], hx, sHx[r * ZS + o_ym], ce);
                     }
                     hxm = hx;
                     hym = hy;
@@ -394,13 +401,13 @@ const SysShape kShapes[2] = {{RingA::TX, RingA::TY, RingA::TZ}, {RingB::TX, Ring
 
 } // namespace
 
-SysShape systolic_shape(int v) { return v == 2 ? systolic_reg_shape() : kShapes[v]; }
+SysShape systolic_shape(int v) { return v >= 2 ? systolic_reg_shape(v - 2) : kShapes[v]; }
 
 size_t systolic_smem_bytes(int v) { return v == 0 ? RingA::smem_bytes() : RingB::smem_bytes(); }
 
 cudaError_t systolic_configure(int v)
 {
-    if (v == 2) return systolic_reg_configure();
+    if (v >= 2) return systolic_reg_configure(v - 2);
     if (v == 0)
         return cudaFuncSetAttribute(systolic_kernel<RingA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)RingA::smem_bytes());
@@ -410,7 +417,7 @@ cudaError_t systolic_configure(int v)
 
 int systolic_max_ctas_per_sm(int v)
 {
-    if (v == 2) return systolic_reg_max_ctas_per_sm();
+    if (v >= 2) return systolic_reg_max_ctas_per_sm(v - 2);
     int n = 0;
     cudaError_t e = v == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_kernel<RingA>,
                                                                           RingA::NTHREADS, RingA::smem_bytes())
@@ -421,7 +428,7 @@ int systolic_max_ctas_per_sm(int v)
 
 cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int v)
 {
-    if (v == 2) return launch_systolic_reg(p, grid, st);
+    if (v >= 2) return launch_systolic_reg(p, grid, st, v - 2);
     if (v == 0)
         systolic_kernel<RingA><<<grid, RingA::NTHREADS, RingA::smem_bytes(), st>>>(p);
     else

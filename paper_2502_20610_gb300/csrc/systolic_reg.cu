@@ -43,45 +43,66 @@ struct RegTile {
     static constexpr int NR = NZ_ + 1;    // plus the shell row -1
     static constexpr int RY = 16, NT = 32 * RY;
     static constexpr int TX = 31, TY = RY - 1, TZ = NZ_;
-    static constexpr int XSR = (NR + 3) / 4 * 4;  // staging rows per field, multiple of 4
-    static constexpr int NXS = TY * 7 * NR;       // x-shell staging entries (15 warps)
-    static constexpr int NXS_PT = (NXS + NT - 1) / NT;
-    static constexpr int NXO = TY * 6 * NZ;       // top x-face entries (15 warps)
-    static constexpr int NXO_PT = (NXO + NT - 1) / NT;
+    static_assert(NR <= 16 && TY <= 16, "cooperative entries: row < 16, warp offset < 16");
     static_assert(NZ % 4 == 0, "top x face is staged with 16-byte stores");
     // shared memory, in floats
     static constexpr int XE_F = RY * NZ * 32;    // one exchanged component
-    static constexpr int XS_F = RY * 6 * XSR;
     static constexpr int XO_F = RY * 6 * NZ;
+    // lower-shell staging filled by 16-byte async copies of aligned 4-float
+    // chunks: rows of SW = 36 floats cover the 32-wide x window from its
+    // 16-byte-aligned start
+    static constexpr int SW = 36, NCX = SW / 4;
+    static constexpr int ZST_F = 7 * RY * SW;        // [field][y row of E window][SW]
+    static constexpr int YST_F = 7 * NR * SW;        // [field][z row][SW]
+    static constexpr int XST_F = TY * 7 * NR * 4;    // [box y row][field][z row][4]
+    static constexpr int NZC = 7 * RY * NCX, NYC = 7 * NR * NCX, NXC = TY * 7 * NR;
+    static constexpr int NCH = NZC + NYC + NXC;
+    static constexpr int NCH_PT = (NCH + NT - 1) / NT;
     static constexpr int CR = 16;                 // coefficient ring rows (>= NR, power of 2)
     static constexpr int CE_F = RY * CR * 32;
     static_assert(CR >= NR, "coefficient ring holds the whole column");
-    static constexpr size_t smem_bytes() { return sizeof(float) * (4 * (size_t)XE_F + XS_F + XO_F + CE_F); }
+    static constexpr size_t smem_bytes()
+    {
+        return sizeof(float) * (4 * (size_t)XE_F + XO_F + CE_F + ZST_F + YST_F + XST_F);
+    }
 };
 
 __device__ __forceinline__ float shfl_from(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
+// 16-byte global -> shared copy that bypasses L1 (data written by other CTAs
+// during the launch); with ok == false nothing is read and zeros are written.
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, bool ok)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <class R>
 __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch P)
 {
-    constexpr int NZ = R::NZ, NR = R::NR, TX = R::TX, TY = R::TY, TZ = R::TZ, XSR = R::XSR;
+    constexpr int NZ = R::NZ, NR = R::NR, TX = R::TX, TY = R::TY, TZ = R::TZ;
     extern __shared__ float4 smem4[];
     float *const sm = reinterpret_cast<float *>(smem4);
     float *const XEx = sm;                 // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
     float *const XEz = XEx + R::XE_F;
     float *const XHx = XEz + R::XE_F;      // [warp][row i-1][lane]: new H rows r = 0..NZ-1
     float *const XHz = XHx + R::XE_F;
-    float *const XS = XHz + R::XE_F;       // [warp][field 0..5][XSR]: x shell column
-    float *const XO = XS + R::XS_F;        // [warp][field 0..5][NZ]: top x face
+    float *const XO = XHz + R::XE_F;       // [warp][field 0..5][NZ]: top x face
     // dt/eps of each column, indexed by physical z mod CR: a cell's coefficient
     // stays in place while the skewed register rows move past it
     float *const CEs = XO + R::XO_F;       // [warp][physical z mod CR][lane]
+    float *const ZST = CEs + R::CE_F;      // lower z shell
+    float *const YST = ZST + R::ZST_F;     // lower y shell
+    float *const XST = YST + R::YST_F;     // lower x shell
     __shared__ int s_ticket, s_abort;
     __shared__ unsigned s_seen[3];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const float ndt = P.neg_dt;
-    const long long sxy = (long long)P.nx * P.ny;
+    const long long sxy = (long long)P.pitch * P.ny;
     // field pointers are read from the kernel parameters where used (they stay
     // in the constant bank instead of taking 14 registers)
 #define F0 P.f[0]
@@ -92,18 +113,13 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
 #define F5 P.f[5]
 #define CE P.ce
 
-    // entries of the cooperative x-shell load / top x-face store handled by
-    // this thread (recomputed where used to keep registers for the column)
-#define XS_ENTRY(q, wi, f, i)                                                 \
-    const int e_##q = tid + (q) * R::NT;                                      \
-    const int wi = e_##q < R::NXS ? e_##q / (7 * NR) : -1;                    \
-    const int f = (e_##q % (7 * NR)) / NR;                                    \
-    const int i = e_##q % NR;
-#define XO_ENTRY(q, wi, f, r)                                                 \
-    const int o_##q = tid + (q) * R::NT;                                      \
-    const int wi = o_##q < R::NXO ? o_##q / (6 * NZ) : -1;                    \
-    const int f = (o_##q % (6 * NZ)) / NZ;                                    \
-    const int r = o_##q % NZ;
+    // Cooperative x-shell load and top x-face store: thread bits pick the
+    // entry (row = tid & 15, field = (tid >> 4) & 7, warp offset = tid >> 7,
+    // plus 4 per pass), so no division is needed.  Field c of the workspace
+    // is fbase + c*fstride (c = 6: dt/eps).
+    const int q_row = tid & 15, q_f = (tid >> 4) & 7, q_w = tid >> 7;
+    float *const FB = P.fbase;
+    const long long FS = P.fstride;
 
     constexpr int CR = R::CR;
     // the tile column of this thread: registers row i <-> r = i-1
@@ -146,7 +162,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
             const int bx = Ax - iv.s, by = Ay - iv.s;
             const int px = bx + ((lane - bx) & 31), py = by + ((w - by) & (R::RY - 1));
             const bool cin = (unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny;
-            const long long col = px + (long long)P.nx * py;
+            const long long col = px + (long long)P.pitch * py;
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
                 const int pz = Az + i - 1 - iv.s + 1;
@@ -172,7 +188,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
             const bool xbox = dx < TX, ybox = dy < TY;
             const bool colin = xbox && ybox && (unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny;
             const int ey_w = (by - 1) & (R::RY - 1);  // warp holding the y shell this step
-            const long long col = px + (long long)P.nx * py;
+            const long long col = px + (long long)P.pitch * py;
             // rows i with physical z = bz + i - 1 inside the domain
             const int i_lo = max(1, 1 - bz), i_hi = min(NR, P.nz - bz + 1);
 
@@ -190,66 +206,51 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
             if (s_abort) { abort = true; break; }
 
             // B. global traffic of this step
-            if (t > iv.s) {  // top x face of step t-1, staged in XO
+            if (t > iv.s && q_row < NZ && q_f < 6) {  // top x face of step t-1, staged in XO
                 const int pbx = bx + 1, pby = by + 1, pbz = bz + 1;
 #pragma unroll
-                for (int q = 0; q < R::NXO_PT; ++q) {
-                    XO_ENTRY(q, wi, f, r)
-                    if (wi >= 0) {
+                for (int q = 0; q < 4; ++q) {
+                    const int wi = q_w + 4 * q;
+                    if (wi < TY) {
                         const int wv = (pby + wi) & (R::RY - 1);
-                        const int qx = pbx + TX - 1, qy = pby + wi, qz = pbz + r;
-                        if (in_dom(P, qx, qy, qz)) P.f[f][gidx(P, qx, qy, qz)] = XO[(wv * 6 + f) * NZ + r];
+                        const int qx = pbx + TX - 1, qy = pby + wi, qz = pbz + q_row;
+                        if (in_dom(P, qx, qy, qz))
+                            FB[q_f * FS + gidx(P, qx, qy, qz)] = XO[(wv * 6 + q_f) * NZ + q_row];
                     }
                 }
             }
-            // lower z shell (level t) for box columns
-            float nz_v[7];
-            {
-                const int pz = bz - 1;
-                if (colin && (unsigned)pz < (unsigned)P.nz) {
-                    const long long g = col + sxy * pz;
-                    nz_v[0] = ld_cg(F0 + g); nz_v[1] = ld_cg(F1 + g); nz_v[2] = ld_cg(F2 + g);
-                    nz_v[3] = ld_cg(F3 + g); nz_v[4] = ld_cg(F4 + g); nz_v[5] = ld_cg(F5 + g);
-                    nz_v[6] = __ldg(CE + g);
-                } else {
+            // lower shells (level t) into shared staging: 16-byte L2-only async
+            // copies of aligned chunks, zero-filled off the domain
+            const int x0 = (bx - 1) & ~3;
 #pragma unroll
-                    for (int c = 0; c < 7; ++c) nz_v[c] = 0.f;
-                }
-            }
-            // lower x shell columns of the 15 warps that are not the y shell
-            float xs_v[R::NXS_PT];
-#pragma unroll
-            for (int q = 0; q < R::NXS_PT; ++q) {
-                XS_ENTRY(q, wi, f, i)
-                xs_v[q] = 0.f;
-                if (wi >= 0) {
-                    const int qx = bx - 1, qy = by + wi, qz = bz + i - 1;
-                    if (in_dom(P, qx, qy, qz)) {
-                        const long long g = gidx(P, qx, qy, qz);
-                        xs_v[q] = f < 6 ? ld_cg(P.f[f] + g) : __ldg(CE + g);
-                    }
-                }
-            }
-            // the y shell warp refills its whole column set (level t)
-            if (w == ey_w) {
-                const int qx = (bx - 1) + ((lane - bx + 1) & 31), qy = by - 1;
-                const bool cin = (unsigned)qx < (unsigned)P.nx && (unsigned)qy < (unsigned)P.ny;
-                const long long c2 = qx + (long long)P.nx * qy;
-#pragma unroll
-                for (int i = 0; i < NR; ++i) {
-                    const int pz = bz + i - 1;
-                    float c = 0.f;
-                    if (cin && (unsigned)pz < (unsigned)P.nz) {
-                        const long long g = c2 + sxy * pz;
-                        ex[i] = ld_cg(F0 + g); ey[i] = ld_cg(F1 + g); ez[i] = ld_cg(F2 + g);
-                        hx[i] = ld_cg(F3 + g); hy[i] = ld_cg(F4 + g); hz[i] = ld_cg(F5 + g);
-                        c = __ldg(CE + g);
+            for (int k = 0; k < R::NCH_PT; ++k) {
+                const int q = tid + k * R::NT;
+                if (q < R::NCH) {
+                    int f, gx, gy, gz;
+                    float *dst;
+                    if (q < R::NZC) {
+                        const int c = q % R::NCX, r = q / R::NCX, yl = r % R::RY;
+                        f = r / R::RY;
+                        gx = x0 + 4 * c; gy = by - 1 + yl; gz = bz - 1;
+                        dst = ZST + (f * R::RY + yl) * R::SW + 4 * c;
+                    } else if (q < R::NZC + R::NYC) {
+                        const int q2 = q - R::NZC, c = q2 % R::NCX, r = q2 / R::NCX, zl = r % NR;
+                        f = r / NR;
+                        gx = x0 + 4 * c; gy = by - 1; gz = bz - 1 + zl;
+                        dst = YST + (f * NR + zl) * R::SW + 4 * c;
                     } else {
-                        ex[i] = ey[i] = ez[i] = hx[i] = hy[i] = hz[i] = 0.f;
+                        const int q3 = q - R::NZC - R::NYC, zl = q3 % NR, r = q3 / NR, wi = r / 7;
+                        f = r % 7;
+                        gx = x0; gy = by + wi; gz = bz - 1 + zl;
+                        dst = XST + ((wi * 7 + f) * NR + zl) * 4;
                     }
-                    CEs[(w * CR + (pz & (CR - 1))) * 32 + lane] = c;
+                    const bool ok = gx >= 0 && gx < P.pitch && (unsigned)gy < (unsigned)P.ny &&
+                                    (unsigned)gz < (unsigned)P.nz;
+                    const float *src = ok ? FB + f * FS + gidx(P, gx, gy, gz) : FB;
+                    cp_async16(dst, src, ok);
                 }
             }
+            cp_async_commit();
 
             // C. H half-step, top-down in place: H[i] <- H[i-1] - dt curl_f(E[i-1], E[i], ...)
             if (w != ey_w) {
@@ -269,50 +270,47 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
                     hy[i] = upd ? nhy : hy[i - 1];
                     hz[i] = upd ? nhz : hz[i - 1];
                 }
-                // row -1 now takes the lower z shell's H (level t)
-                hx[0] = nz_v[3]; hy[0] = nz_v[4]; hz[0] = nz_v[5];
             }
+            cp_async_wait_all();
+            __syncthreads();  // the staged shells are visible
 
-            // D. publish new H rows for the warp above's E half-step; stage the x shell
+            // D. refills from the staged shells, then publish new H rows for the
+            //    warp above's E half-step
+            const int xe = (bx - 1) - x0;  // x offset of the shell column in its chunk
+            if (w == ey_w) {  // the y shell warp takes its whole column set (level t)
+                const int xl = (bx - 1) + ((lane - bx + 1) & 31) - x0;
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    ex[i] = YST[(0 * NR + i) * R::SW + xl]; ey[i] = YST[(1 * NR + i) * R::SW + xl];
+                    ez[i] = YST[(2 * NR + i) * R::SW + xl]; hx[i] = YST[(3 * NR + i) * R::SW + xl];
+                    hy[i] = YST[(4 * NR + i) * R::SW + xl]; hz[i] = YST[(5 * NR + i) * R::SW + xl];
+                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YST[(6 * NR + i) * R::SW + xl];
+                }
+            } else if (xbox) {  // row -1 takes the lower z shell's H and coefficient
+                const int o = (dy + 1) * R::SW + (px - x0);
+                hx[0] = ZST[3 * R::RY * R::SW + o];
+                hy[0] = ZST[4 * R::RY * R::SW + o];
+                hz[0] = ZST[5 * R::RY * R::SW + o];
+                CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZST[6 * R::RY * R::SW + o];
+            } else {  // the lane leaving the tile in x takes the x shell's H and coefficient
+                const float *xs = XST + dy * 7 * NR * 4 + xe;
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    hx[i] = xs[(3 * NR + i) * 4];
+                    hy[i] = xs[(4 * NR + i) * 4];
+                    hz[i] = xs[(5 * NR + i) * 4];
+                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xs[(6 * NR + i) * 4];
+                }
+            }
 #pragma unroll
             for (int i = 1; i < NR; ++i) {
                 XHx[(w * NZ + (i - 1)) * 32 + lane] = hx[i];
                 XHz[(w * NZ + (i - 1)) * 32 + lane] = hz[i];
             }
-#pragma unroll
-            for (int q = 0; q < R::NXS_PT; ++q) {
-                XS_ENTRY(q, wi, f, i)
-                if (wi >= 0) {
-                    const int wv = (by + wi) & (R::RY - 1);
-                    if (f < 6)
-                        XS[(wv * 6 + f) * XSR + i] = xs_v[q];
-                    else
-                        CEs[(wv * CR + ((bz + i - 1) & (CR - 1))) * 32 + ((bx - 1) & 31)] = xs_v[q];
-                }
-            }
-            if (w != ey_w && xbox) CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = nz_v[6];
             __syncthreads();  // B2
             if (t > iv.s && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)t);  // level t-1 done
 
             if (w != ey_w) {
-                // E. the lane leaving the tile in x takes the x shell's H
-                const float *xs = XS + w * 6 * XSR;
-                if (!xbox) {
-#pragma unroll
-                    for (int k = 0; k < XSR / 4; ++k) {
-                        const float4 a = *reinterpret_cast<const float4 *>(xs + 3 * XSR + 4 * k);
-                        const float4 b = *reinterpret_cast<const float4 *>(xs + 4 * XSR + 4 * k);
-                        const float4 c = *reinterpret_cast<const float4 *>(xs + 5 * XSR + 4 * k);
-                        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w},
-                                    cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (4 * k + u < NR) {
-                                hx[4 * k + u] = av[u]; hy[4 * k + u] = bv[u]; hz[4 * k + u] = cv[u];
-                            }
-                        }
-                    }
-                }
                 // F. E half-step, top-down in place: E[i] <- E[i-1] + ce curl_b(H[i], H[i-1], ...)
                 const int wm = (w - 1) & (R::RY - 1);
                 const int src = (lane - 1) & 31;
@@ -333,23 +331,18 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
                     ey[i] = (in && uy && kz) ? ney : ey[i - 1];
                     ez[i] = (in && uz) ? nez : ez[i - 1];
                 }
-                // row -1 takes the lower z shell's E and coefficient (level t)
-                ex[0] = nz_v[0]; ey[0] = nz_v[1]; ez[0] = nz_v[2];
-                // the x lane takes the rest of its shell column
-                if (!xbox) {
+                if (xbox) {  // row -1 takes the lower z shell's E (level t)
+                    const int o = (dy + 1) * R::SW + (px - x0);
+                    ex[0] = ZST[0 * R::RY * R::SW + o];
+                    ey[0] = ZST[1 * R::RY * R::SW + o];
+                    ez[0] = ZST[2 * R::RY * R::SW + o];
+                } else {  // the x lane takes the rest of its shell column
+                    const float *xs = XST + dy * 7 * NR * 4 + xe;
 #pragma unroll
-                    for (int k = 0; k < XSR / 4; ++k) {
-                        const float4 a = *reinterpret_cast<const float4 *>(xs + 0 * XSR + 4 * k);
-                        const float4 b = *reinterpret_cast<const float4 *>(xs + 1 * XSR + 4 * k);
-                        const float4 c = *reinterpret_cast<const float4 *>(xs + 2 * XSR + 4 * k);
-                        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w},
-                                    cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (4 * k + u < NR) {
-                                ex[4 * k + u] = av[u]; ey[4 * k + u] = bv[u]; ez[4 * k + u] = cv[u];
-                            }
-                        }
+                    for (int i = 0; i < NR; ++i) {
+                        ex[i] = xs[(0 * NR + i) * 4];
+                        ey[i] = xs[(1 * NR + i) * 4];
+                        ez[i] = xs[(2 * NR + i) * 4];
                     }
                 }
             }
@@ -427,15 +420,16 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
         if (abort) break;
         // the last step's staged top x face, then its progress
         __syncthreads();
-        if (iv.e < P.T - 1) {
+        if (iv.e < P.T - 1 && q_row < NZ && q_f < 6) {
             const int pbx = Ax - iv.e, pby = Ay - iv.e, pbz = Az - iv.e;
 #pragma unroll
-            for (int q = 0; q < R::NXO_PT; ++q) {
-                XO_ENTRY(q, wi, f, r)
-                if (wi >= 0) {
+            for (int q = 0; q < 4; ++q) {
+                const int wi = q_w + 4 * q;
+                if (wi < TY) {
                     const int wv = (pby + wi) & (R::RY - 1);
-                    const int qx = pbx + TX - 1, qy = pby + wi, qz = pbz + r;
-                    if (in_dom(P, qx, qy, qz)) P.f[f][gidx(P, qx, qy, qz)] = XO[(wv * 6 + f) * NZ + r];
+                    const int qx = pbx + TX - 1, qy = pby + wi, qz = pbz + q_row;
+                    if (in_dom(P, qx, qy, qz))
+                        FB[q_f * FS + gidx(P, qx, qy, qz)] = XO[(wv * 6 + q_f) * NZ + q_row];
                 }
             }
         }
@@ -451,30 +445,41 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
 #undef F4
 #undef F5
 #undef CE
-#undef XS_ENTRY
-#undef XO_ENTRY
 
-using RegA = RegTile<12>;
+using RegA = RegTile<12>;  // 31 x 15 x 12
+using RegB = RegTile<8>;   // 31 x 15 x 8
 
 } // namespace
 
-SysShape systolic_reg_shape() { return {RegA::TX, RegA::TY, RegA::TZ}; }
-
-cudaError_t systolic_reg_configure()
+SysShape systolic_reg_shape(int k)
 {
-    return cudaFuncSetAttribute(systolic_reg_kernel<RegA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)RegA::smem_bytes());
+    return k == 0 ? SysShape{RegA::TX, RegA::TY, RegA::TZ} : SysShape{RegB::TX, RegB::TY, RegB::TZ};
 }
 
-int systolic_reg_max_ctas_per_sm()
+cudaError_t systolic_reg_configure(int k)
+{
+    if (k == 0)
+        return cudaFuncSetAttribute(systolic_reg_kernel<RegA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)RegA::smem_bytes());
+    return cudaFuncSetAttribute(systolic_reg_kernel<RegB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RegB::smem_bytes());
+}
+
+int systolic_reg_max_ctas_per_sm(int k)
 {
     int n = 0;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_reg_kernel<RegA>, RegA::NT,
-                                                         RegA::smem_bytes()) == cudaSuccess ? n : 0;
+    cudaError_t e = k == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_reg_kernel<RegA>, RegA::NT,
+                                                                          RegA::smem_bytes())
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_reg_kernel<RegB>, RegB::NT,
+                                                                          RegB::smem_bytes());
+    return e == cudaSuccess ? n : 0;
 }
 
-cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st)
+cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k)
 {
-    systolic_reg_kernel<RegA><<<grid, RegA::NT, RegA::smem_bytes(), st>>>(p);
+    if (k == 0)
+        systolic_reg_kernel<RegA><<<grid, RegA::NT, RegA::smem_bytes(), st>>>(p);
+    else
+        systolic_reg_kernel<RegB><<<grid, RegB::NT, RegB::smem_bytes(), st>>>(p);
     return cudaGetLastError();
 }

@@ -108,7 +108,8 @@ def _check(status, what):
 
 
 #: systolic tile shapes (updated cells x, y, z) the library is built with
-TILES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15), "31x15x12": (31, 15, 12)}
+TILES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15), "31x15x12": (31, 15, 12),
+         "31x15x8": (31, 15, 8)}
 
 
 def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,

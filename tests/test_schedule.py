@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 TX, TY, TZ = 31, 15, 15
-SHAPES = [(31, 15, 15), (31, 7, 15), (31, 15, 12)]  # the tile shapes the library is built with
+SHAPES = [(31, 15, 15), (31, 7, 15), (31, 15, 12), (31, 15, 8)]  # the tile shapes the library is built with
 
 
 def interval(I, J, K, N, T, n=(TX, TY, TZ)):
