@@ -4,6 +4,8 @@
 #include "fdtd.h"
 #include "internal.h"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -168,6 +170,43 @@ void build_tiles(const fdtd_grid &g, const Layout &L, int order, unsigned seed,
 
 } // namespace
 
+// Tensor-map encoder of the CUDA driver, fetched once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+bool encode_shell_maps(CUtensorMap tm[3][7], float *fbase, long long fstride, int nx, int ny, int nz,
+                       int pitch, int nr)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || fstride <= 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4u, (cuuint64_t)pitch * (cuuint64_t)ny * 4u};
+    // lower z shell {36,16,1}, lower y shell {36,1,nr}, lower x shell {4,16,nr}
+    const cuuint32_t box[3][3] = {{36, 16, 1}, {36, 1, (cuuint32_t)nr}, {4, 16, (cuuint32_t)nr}};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int s = 0; s < 3; ++s)
+        for (int a = 0; a < 7; ++a) {
+            CUresult r = enc(&tm[s][a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, fbase + a * fstride, dims, strides,
+                             box[s], estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return false;
+        }
+    return true;
+}
+
 // Tile hand-out order of the systolic scheme for one launch of up to T
 // steps with tile shape `variant` (same rule as a handle's schedule), for
 // callers that manage their own scratch.
@@ -213,6 +252,7 @@ struct fdtd_sim {
     int dbg_kind;
     long long dbg_ticket, dbg_param, dbg_param2;
     bool failed;
+    CUtensorMap tm[3][7];  // shell maps of the register kernel
 };
 
 namespace {
@@ -339,6 +379,12 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
         const int per_sm = systolic_max_ctas_per_sm(L.variant);
         if (per_sm < 1) return fail(FDTD_ERR_UNSUPPORTED);
         h->max_ctas = sms * per_sm;
+        if (L.variant >= 2) {
+            const long long fstride = (long long)(L.fields[1] - L.fields[0]) / (long long)sizeof(float);
+            if (!encode_shell_maps(h->tm, h->f[0], fstride, grid->nx, grid->ny, grid->nz, L.pitch,
+                                   systolic_reg_rows(L.variant - 2)))
+                return fail(FDTD_ERR_UNSUPPORTED);
+        }
         fdtd_status st = upload_tiles(h, 0, 0);
         if (st != FDTD_OK) return fail(st);
     }
@@ -437,6 +483,7 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         p.dbg_param = h->dbg_param;
         p.dbg_param2 = h->dbg_param2;
         p.src = h->src;
+        if (h->L.variant >= 2) std::memcpy(p.tm, h->tm, sizeof(p.tm));
         const int grid = (int)std::max<long long>(1, std::min<long long>(p.ntiles, h->max_ctas));
         CK(launch_systolic(p, grid, h->stream, h->L.variant));
         h->launches += 1;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (type only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 #include <vector>
 
@@ -65,7 +66,16 @@ struct SysLaunch {
     int dbg_kind;
     long long dbg_ticket, dbg_param, dbg_param2;
     SrcSet src;
+    // bulk-tensor (TMA) maps of the 6 fields and dt/eps, for the register
+    // kernel's shell staging: [shape][array], shapes = lower z, y, x shell
+    CUtensorMap tm[3][7];
 };
+
+// Encode the 21 shell maps of the register kernel with `nr` z rows per
+// column; fbase/fstride/pitch as in SysLaunch.  Returns false on failure.
+bool encode_shell_maps(CUtensorMap tm[3][7], float *fbase, long long fstride, int nx, int ny, int nz,
+                       int pitch, int nr);
+int systolic_reg_rows(int k);
 
 size_t systolic_smem_bytes(int variant);
 cudaError_t systolic_configure(int variant);

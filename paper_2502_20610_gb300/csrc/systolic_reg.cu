@@ -48,16 +48,16 @@ struct RegTile {
     // shared memory, in floats
     static constexpr int XE_F = RY * NZ * 32;    // one exchanged component
     static constexpr int XO_F = RY * 6 * NZ;
-    // lower-shell staging filled by 16-byte async copies of aligned 4-float
-    // chunks: rows of SW = 36 floats cover the 32-wide x window from its
-    // 16-byte-aligned start
-    static constexpr int SW = 36, NCX = SW / 4;
-    static constexpr int ZST_F = 7 * RY * SW;        // [field][y row of E window][SW]
-    static constexpr int YST_F = 7 * NR * SW;        // [field][z row][SW]
-    static constexpr int XST_F = TY * 7 * NR * 4;    // [box y row][field][z row][4]
-    static constexpr int NZC = 7 * RY * NCX, NYC = 7 * NR * NCX, NXC = TY * 7 * NR;
-    static constexpr int NCH = NZC + NYC + NXC;
-    static constexpr int NCH_PT = (NCH + NT - 1) / NT;
+    // lower-shell staging, filled per step by bulk tensor copies (TMA) of
+    // boxes whose x start is rounded down to 16 bytes: SW = 36 floats cover
+    // the 32-wide x window; every box starts on a 128-byte boundary
+    static constexpr int SW = 36;
+    static constexpr int ZB = RY * SW;                       // z shell box {36,16,1}: [y][x]
+    static constexpr int YB = (NR * SW * 4 + 127) / 128 * 32; // y shell box {36,1,NR}: [z][x], padded
+    static constexpr int XB = NR * 16 * 4;                   // x shell box {4,16,NR}: [z][y][x]
+    static_assert((ZB * 4) % 128 == 0 && (XB * 4) % 128 == 0, "boxes stay 128-byte aligned");
+    static constexpr int ZST_F = 7 * ZB, YST_F = 7 * YB, XST_F = 7 * XB;
+    static constexpr unsigned TMA_BYTES = 4u * 7u * (RY * SW + NR * SW + NR * 16 * 4);
     static constexpr int CR = 16;                 // coefficient ring rows (>= NR, power of 2)
     static constexpr int CE_F = RY * CR * 32;
     static_assert(CR >= NR, "coefficient ring holds the whole column");
@@ -69,24 +69,54 @@ struct RegTile {
 
 __device__ __forceinline__ float shfl_from(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
-// 16-byte global -> shared copy that bypasses L1 (data written by other CTAs
-// during the launch); with ok == false nothing is read and zeros are written.
-__device__ __forceinline__ void cp_async16(float *dst, const float *src, bool ok)
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Bulk tensor copy of one 3D box (TMA) into shared memory, completing on an
+// mbarrier; elements outside the tensor are written as zero.
+__device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                        unsigned long long *bar)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0)
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Bounded wait for phase `parity` of the staging barrier.  Returns false if
+// the wait ran past the launch's timeout (the error word is then set).
+__device__ bool wait_stage(const SysLaunch &P, unsigned long long *bar, unsigned parity, int ticket)
+{
+    unsigned long long t0 = 0;
+    for (int it = 0;; ++it) {
+        unsigned done;
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+                     " selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (done) return true;
+        const unsigned long long now = globaltimer();
+        if (it == 0) {
+            t0 = now;
+        } else if (now - t0 > (unsigned long long)P.timeout_ns) {
+            if (atomicCAS(P.ctrl + 1, DEV_OK, DEV_ERR_TIMEOUT) == DEV_OK) {
+                P.ctrl[2] = ticket;
+                P.ctrl[3] = -1;
+            }
+            return false;
+        }
+    }
+}
 
 template <class R>
-__global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch P)
+__global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_constant__ SysLaunch P)
 {
     constexpr int NZ = R::NZ, NR = R::NR, TX = R::TX, TY = R::TY, TZ = R::TZ;
-    extern __shared__ float4 smem4[];
+    extern __shared__ __align__(1024) float4 smem4[];
     float *const sm = reinterpret_cast<float *>(smem4);
-    float *const XEx = sm;                 // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
+    // staging boxes first: the dynamic shared memory base is 1024-byte aligned
+    float *const ZST = sm;                 // lower z shell
+    float *const YST = ZST + R::ZST_F;     // lower y shell
+    float *const XST = YST + R::YST_F;     // lower x shell
+    float *const XEx = XST + R::XST_F;     // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
     float *const XEz = XEx + R::XE_F;
     float *const XHx = XEz + R::XE_F;      // [warp][row i-1][lane]: new H rows r = 0..NZ-1
     float *const XHz = XHx + R::XE_F;
@@ -94,10 +124,8 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
     // dt/eps of each column, indexed by physical z mod CR: a cell's coefficient
     // stays in place while the skewed register rows move past it
     float *const CEs = XO + R::XO_F;       // [warp][physical z mod CR][lane]
-    float *const ZST = CEs + R::CE_F;      // lower z shell
-    float *const YST = ZST + R::ZST_F;     // lower y shell
-    float *const XST = YST + R::YST_F;     // lower x shell
     __shared__ int s_ticket, s_abort;
+    __shared__ alignas(8) unsigned long long s_bar;  // staging barrier: one phase per step
     __shared__ unsigned s_seen[3];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -122,6 +150,12 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
     const long long FS = P.fstride;
 
     constexpr int CR = R::CR;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned stage_phase = 0;  // completed phases of s_bar
     // the tile column of this thread: registers row i <-> r = i-1
     float ex[NR], ey[NR], ez[NR], hx[NR], hy[NR], hz[NR];
 
@@ -219,38 +253,21 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
                     }
                 }
             }
-            // lower shells (level t) into shared staging: 16-byte L2-only async
-            // copies of aligned chunks, zero-filled off the domain
+            // lower shells (level t) into shared staging: 21 bulk tensor copies
+            // issued by one thread (x start rounded down to 16 bytes; zero fill
+            // off the domain)
             const int x0 = (bx - 1) & ~3;
+            if (tid == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_bar)),
+                             "r"(R::TMA_BYTES) : "memory");
 #pragma unroll
-            for (int k = 0; k < R::NCH_PT; ++k) {
-                const int q = tid + k * R::NT;
-                if (q < R::NCH) {
-                    int f, gx, gy, gz;
-                    float *dst;
-                    if (q < R::NZC) {
-                        const int c = q % R::NCX, r = q / R::NCX, yl = r % R::RY;
-                        f = r / R::RY;
-                        gx = x0 + 4 * c; gy = by - 1 + yl; gz = bz - 1;
-                        dst = ZST + (f * R::RY + yl) * R::SW + 4 * c;
-                    } else if (q < R::NZC + R::NYC) {
-                        const int q2 = q - R::NZC, c = q2 % R::NCX, r = q2 / R::NCX, zl = r % NR;
-                        f = r / NR;
-                        gx = x0 + 4 * c; gy = by - 1; gz = bz - 1 + zl;
-                        dst = YST + (f * NR + zl) * R::SW + 4 * c;
-                    } else {
-                        const int q3 = q - R::NZC - R::NYC, zl = q3 % NR, r = q3 / NR, wi = r / 7;
-                        f = r % 7;
-                        gx = x0; gy = by + wi; gz = bz - 1 + zl;
-                        dst = XST + ((wi * 7 + f) * NR + zl) * 4;
-                    }
-                    const bool ok = gx >= 0 && gx < P.pitch && (unsigned)gy < (unsigned)P.ny &&
-                                    (unsigned)gz < (unsigned)P.nz;
-                    const float *src = ok ? FB + f * FS + gidx(P, gx, gy, gz) : FB;
-                    cp_async16(dst, src, ok);
+                for (int f = 0; f < 7; ++f) {
+                    tma_box(ZST + f * R::ZB, &P.tm[0][f], x0, by - 1, bz - 1, &s_bar);
+                    tma_box(YST + f * R::YB, &P.tm[1][f], x0, by - 1, bz - 1, &s_bar);
+                    tma_box(XST + f * R::XB, &P.tm[2][f], x0, by, bz - 1, &s_bar);
                 }
             }
-            cp_async_commit();
 
             // C. H half-step, top-down in place: H[i] <- H[i-1] - dt curl_f(E[i-1], E[i], ...)
             if (w != ey_w) {
@@ -271,8 +288,10 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
                     hz[i] = upd ? nhz : hz[i - 1];
                 }
             }
-            cp_async_wait_all();
+            if (!wait_stage(P, &s_bar, stage_phase & 1u, ticket)) s_abort = 1;
+            ++stage_phase;
             __syncthreads();  // the staged shells are visible
+            if (s_abort) { abort = true; break; }
 
             // D. refills from the staged shells, then publish new H rows for the
             //    warp above's E half-step
@@ -281,25 +300,25 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
                 const int xl = (bx - 1) + ((lane - bx + 1) & 31) - x0;
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
-                    ex[i] = YST[(0 * NR + i) * R::SW + xl]; ey[i] = YST[(1 * NR + i) * R::SW + xl];
-                    ez[i] = YST[(2 * NR + i) * R::SW + xl]; hx[i] = YST[(3 * NR + i) * R::SW + xl];
-                    hy[i] = YST[(4 * NR + i) * R::SW + xl]; hz[i] = YST[(5 * NR + i) * R::SW + xl];
-                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YST[(6 * NR + i) * R::SW + xl];
+                    ex[i] = YST[0 * R::YB + i * R::SW + xl]; ey[i] = YST[1 * R::YB + i * R::SW + xl];
+                    ez[i] = YST[2 * R::YB + i * R::SW + xl]; hx[i] = YST[3 * R::YB + i * R::SW + xl];
+                    hy[i] = YST[4 * R::YB + i * R::SW + xl]; hz[i] = YST[5 * R::YB + i * R::SW + xl];
+                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YST[6 * R::YB + i * R::SW + xl];
                 }
             } else if (xbox) {  // row -1 takes the lower z shell's H and coefficient
                 const int o = (dy + 1) * R::SW + (px - x0);
-                hx[0] = ZST[3 * R::RY * R::SW + o];
-                hy[0] = ZST[4 * R::RY * R::SW + o];
-                hz[0] = ZST[5 * R::RY * R::SW + o];
-                CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZST[6 * R::RY * R::SW + o];
+                hx[0] = ZST[3 * R::ZB + o];
+                hy[0] = ZST[4 * R::ZB + o];
+                hz[0] = ZST[5 * R::ZB + o];
+                CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZST[6 * R::ZB + o];
             } else {  // the lane leaving the tile in x takes the x shell's H and coefficient
-                const float *xs = XST + dy * 7 * NR * 4 + xe;
+                const float *xs = XST + dy * 4 + xe;
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
-                    hx[i] = xs[(3 * NR + i) * 4];
-                    hy[i] = xs[(4 * NR + i) * 4];
-                    hz[i] = xs[(5 * NR + i) * 4];
-                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xs[(6 * NR + i) * 4];
+                    hx[i] = xs[3 * R::XB + i * 64];
+                    hy[i] = xs[4 * R::XB + i * 64];
+                    hz[i] = xs[5 * R::XB + i * 64];
+                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xs[6 * R::XB + i * 64];
                 }
             }
 #pragma unroll
@@ -333,16 +352,16 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const SysLaunch 
                 }
                 if (xbox) {  // row -1 takes the lower z shell's E (level t)
                     const int o = (dy + 1) * R::SW + (px - x0);
-                    ex[0] = ZST[0 * R::RY * R::SW + o];
-                    ey[0] = ZST[1 * R::RY * R::SW + o];
-                    ez[0] = ZST[2 * R::RY * R::SW + o];
+                    ex[0] = ZST[0 * R::ZB + o];
+                    ey[0] = ZST[1 * R::ZB + o];
+                    ez[0] = ZST[2 * R::ZB + o];
                 } else {  // the x lane takes the rest of its shell column
-                    const float *xs = XST + dy * 7 * NR * 4 + xe;
+                    const float *xs = XST + dy * 4 + xe;
 #pragma unroll
                     for (int i = 0; i < NR; ++i) {
-                        ex[i] = xs[(0 * NR + i) * 4];
-                        ey[i] = xs[(1 * NR + i) * 4];
-                        ez[i] = xs[(2 * NR + i) * 4];
+                        ex[i] = xs[0 * R::XB + i * 64];
+                        ey[i] = xs[1 * R::XB + i * 64];
+                        ez[i] = xs[2 * R::XB + i * 64];
                     }
                 }
             }
@@ -450,6 +469,8 @@ using RegA = RegTile<12>;  // 31 x 15 x 12
 using RegB = RegTile<8>;   // 31 x 15 x 8
 
 } // namespace
+
+int systolic_reg_rows(int k) { return k == 0 ? RegA::NR : RegB::NR; }
 
 SysShape systolic_reg_shape(int k)
 {
