@@ -32,8 +32,20 @@ WAVELENGTH = 20.0
 # Algorithmic bytes per cell-step (fields FP32, coefficient FP32):
 STREAM_BYTES = 48.0                        # ideal one-pass stream: 6 read + 6 written
 NAIVE_BYTES = 76.0                         # two kernels: H 24R+12W, E 24R+4R+12W
-SHELL_CELLS, TILE_CELLS = 1217, 6975       # 32x16x16 ring, 31x15x15 updated
-SYSTOLIC_BYTES = SHELL_CELLS / TILE_CELLS * 52.0   # shell E,H read+write and eps read
+# systolic: per tile step the lower shell is read (E, H, dt/eps: 28 B/cell) and
+# the top faces written (E, H: 24 B/cell); per updated cell that is
+# (shell + top) traffic / updated cells.  Tiles: updated (tx, ty, tz), ring
+# (tx+1, ty+1, tz+1); the library's default is 31 x 15 x 12.
+TILE_SHAPES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15), "31x15x12": (31, 15, 12), "31x15x8": (31, 15, 8)}
+DEFAULT_TILE = "31x15x12"
+
+
+def systolic_bytes(tile):
+    tx, ty, tz = TILE_SHAPES[tile]
+    upd = tx * ty * tz
+    shell = (tx + 1) * (ty + 1) * (tz + 1) - upd
+    top = upd - (tx - 1) * (ty - 1) * (tz - 1)
+    return (28.0 * shell + 24.0 * top) / upd
 
 
 def load_peaks():
@@ -302,7 +314,9 @@ def main():
     peak, peak_kind = load_peaks()
     per_launch_s = elapsed / max(launches, 1)
     cell_steps_per_launch = cells * STEPS_PER_CALL * args.steps / max(launches, 1)
-    achieved = SYSTOLIC_BYTES * cell_steps_per_launch / per_launch_s / 1e9
+    tile = args.tile or DEFAULT_TILE
+    sys_bytes = systolic_bytes(tile) if args.scheme == "systolic" else NAIVE_BYTES
+    achieved = sys_bytes * cell_steps_per_launch / per_launch_s / 1e9
     line = {
         "metric": "GCUPS of 3D Yee update, systolic vs naive kernel, FP32 & FP16-stored, 1 GB300",
         "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -311,8 +325,8 @@ def main():
         "scheme": args.scheme,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "systolic_kernel",
-                     "algorithmic_bytes_per_cell_step": round(SYSTOLIC_BYTES, 3)},
+                     "kernel": "systolic_reg_kernel" if args.scheme == "systolic" else "naive_h/e",
+                     "tile": tile, "algorithmic_bytes_per_cell_step": round(sys_bytes, 3)},
         "stream_roofline": {"bytes_per_cell_step": STREAM_BYTES,
                             "bound_gcups": peak / STREAM_BYTES,
                             "frac": gcups / world / (peak / STREAM_BYTES), "peak_kind": peak_kind},

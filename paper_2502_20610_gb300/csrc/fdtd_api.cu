@@ -33,7 +33,7 @@ struct Layout {
 
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-constexpr int DEFAULT_VARIANT = 0;  // 31 x 15 x 15 measured faster than 31 x 7 x 15 (104 vs 79 GCUPS)
+constexpr int DEFAULT_VARIANT = 2;  // register-resident 31 x 15 x 12 with TMA shells: fastest measured
 
 // Tile shape requested in coeffs.tile (0,0,0 = default) -> variant, or -1.
 int pick_variant(const fdtd_coeffs &c)
