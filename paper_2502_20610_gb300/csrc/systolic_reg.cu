@@ -239,7 +239,26 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             __syncthreads();  // B1
             if (s_abort) { abort = true; break; }
 
-            // B. global traffic of this step
+            // B. the warp whose y slot leaves the tile this step is idle during
+            //    the H half-step: it stores last step's top y face, which its
+            //    registers still hold; all threads store the staged top x face
+            if (w == ey_w && t > iv.s) {
+                const int pbx = bx + 1, pby = by + 1, pbz = bz + 1;  // box corner of step t-1
+                const int pdx = (lane - pbx) & 31;
+                const int qx = pbx + pdx, qy = pby + TY - 1;
+                if (pdx < TX && (unsigned)qx < (unsigned)P.nx && (unsigned)qy < (unsigned)P.ny) {
+                    const long long c2 = qx + (long long)P.pitch * qy;
+#pragma unroll
+                    for (int i = 1; i < NR; ++i) {
+                        const int qz = pbz + i - 1;
+                        if ((unsigned)qz < (unsigned)P.nz) {
+                            const long long g = c2 + sxy * qz;
+                            F0[g] = ex[i]; F1[g] = ey[i]; F2[g] = ez[i];
+                            F3[g] = hx[i]; F4[g] = hy[i]; F5[g] = hz[i];
+                        }
+                    }
+                }
+            }
             if (t > iv.s && q_row < NZ && q_f < 6) {  // top x face of step t-1, staged in XO
                 const int pbx = bx + 1, pby = by + 1, pbz = bz + 1;
 #pragma unroll
@@ -401,16 +420,8 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 }
             } else {
                 if (colin) {
-                    if (dy == TY - 1) {  // top y face: the whole column
-#pragma unroll
-                        for (int i = 1; i < NR; ++i) {
-                            if (i >= i_lo && i < i_hi) {
-                                const long long g = col + sxy * (bz + i - 1);
-                                F0[g] = ex[i]; F1[g] = ey[i]; F2[g] = ez[i];
-                                F3[g] = hx[i]; F4[g] = hy[i]; F5[g] = hz[i];
-                            }
-                        }
-                    } else if (NR - 1 >= i_lo && NR - 1 < i_hi) {  // top z face
+                    // (the top y face is stored next step by the warp holding it)
+                    if (NR - 1 >= i_lo && NR - 1 < i_hi) {  // top z face
                         const long long g = col + sxy * (bz + NR - 2);
                         F0[g] = ex[NR - 1]; F1[g] = ey[NR - 1]; F2[g] = ez[NR - 1];
                         F3[g] = hx[NR - 1]; F4[g] = hy[NR - 1]; F5[g] = hz[NR - 1];
@@ -437,8 +448,25 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             }
         }
         if (abort) break;
-        // the last step's staged top x face, then its progress
+        // the last step's top y face and staged top x face, then its progress
         __syncthreads();
+        if (iv.e < P.T - 1) {
+            const int pbx = Ax - iv.e, pby = Ay - iv.e, pbz = Az - iv.e;
+            const int pdx = (lane - pbx) & 31, pdy = (w - pby) & (R::RY - 1);
+            const int qx = pbx + pdx, qy = pby + pdy;
+            if (pdy == TY - 1 && pdx < TX && (unsigned)qx < (unsigned)P.nx && (unsigned)qy < (unsigned)P.ny) {
+                const long long c2 = qx + (long long)P.pitch * qy;
+#pragma unroll
+                for (int i = 1; i < NR; ++i) {
+                    const int qz = pbz + i - 1;
+                    if ((unsigned)qz < (unsigned)P.nz) {
+                        const long long g = c2 + sxy * qz;
+                        F0[g] = ex[i]; F1[g] = ey[i]; F2[g] = ez[i];
+                        F3[g] = hx[i]; F4[g] = hy[i]; F5[g] = hz[i];
+                    }
+                }
+            }
+        }
         if (iv.e < P.T - 1 && q_row < NZ && q_f < 6) {
             const int pbx = Ax - iv.e, pby = Ay - iv.e, pbz = Az - iv.e;
 #pragma unroll
