@@ -1,4 +1,5 @@
-"""Benchmark: GCUPS of the 3D Yee update, systolic vs naive schedule, FP32, 1 GB300.
+"""Benchmark: GCUPS of the 3D Yee update, systolic vs naive schedule, FP32 and
+16-bit field storage, 1 GB300.
 
 Workload (one bench "step" = one fdtd_step(2000) call of the whole hot path):
 256^3 grid, seeded Si/SiO2 permittivity map (eps 2.1 background with 8-20
@@ -7,6 +8,9 @@ eps 12.1 slabs of 10x10 cross-section), PEC walls, sinusoidal point Jz dipole
 GCUPS = cells * steps / seconds / 1e9.  The 470 MB of device state is larger
 than L2 (129 MB), so no L2 flush is needed between timed calls.
 
+The headline value is the FP32 systolic schedule; the line also carries the
+naive schedule and both schedules with FP16 and BF16 field storage (FP32
+arithmetic) on the same workload.
 Prints ONE JSON line.  `--impl reference` times the FP64 CPU oracle instead
 (the reference arm), on a bounded sample of the same workload.
 Multi-GPU (torchrun): independent replicas, one per GPU (weak scaling; the
@@ -29,13 +33,11 @@ sys.path.insert(0, ROOT)
 GRID = (256, 256, 256)
 STEPS_PER_CALL = 2000
 WAVELENGTH = 20.0
-# Algorithmic bytes per cell-step (fields FP32, coefficient FP32):
-STREAM_BYTES = 48.0                        # ideal one-pass stream: 6 read + 6 written
-NAIVE_BYTES = 76.0                         # two kernels: H 24R+12W, E 24R+4R+12W
-# systolic: per tile step the lower shell is read (E, H, dt/eps: 28 B/cell) and
-# the top faces written (E, H: 24 B/cell); per updated cell that is
-# (shell + top) traffic / updated cells.  Tiles: updated (tx, ty, tz), ring
-# (tx+1, ty+1, tz+1); the library's default is 31 x 15 x 12.
+# Algorithmic bytes per cell-step: the streaming bound reads and writes the
+# six fields once (12 x element bytes: 48 B FP32, 24 B 16-bit); the naive
+# schedule and the systolic tiles are modelled in naive_bytes/systolic_bytes.
+# Tiles: updated (tx, ty, tz), ring (tx+1, ty+1, tz+1); the library's default
+# is 31 x 15 x 12.
 TILE_SHAPES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15), "31x15x12": (31, 15, 12), "31x15x8": (31, 15, 8)}
 DEFAULT_TILE = "31x15x12"
 
@@ -47,12 +49,24 @@ DEFAULT_TILE = "31x15x12"
 MEASURED_TRAFFIC = {"31x15x12": 7.53}
 
 
-def systolic_bytes(tile):
+STORAGE_BYTES = {"f32": 4, "f16": 2, "bf16": 2}
+
+
+def systolic_bytes(tile, eb=4):
+    """Algorithmic bytes per cell update of the systolic kernel: per tile step
+    the lower shell is read (6 fields of eb bytes and the FP32 dt/eps) and
+    the top faces are written (6 fields), divided by the updated cells."""
     tx, ty, tz = TILE_SHAPES[tile]
     upd = tx * ty * tz
     shell = (tx + 1) * (ty + 1) * (tz + 1) - upd
     top = upd - (tx - 1) * (ty - 1) * (tz - 1)
-    return (28.0 * shell + 24.0 * top) / upd
+    return ((6 * eb + 4.0) * shell + 6.0 * eb * top) / upd
+
+
+def naive_bytes(eb=4):
+    """Two kernels per step: H reads 6 fields and writes 3; E reads 6 fields
+    and dt/eps and writes 3."""
+    return 6.0 * eb + 3.0 * eb + 6.0 * eb + 4.0 + 3.0 * eb
 
 
 def load_peaks():
@@ -207,12 +221,38 @@ def run_reference(args, world, rank):
     return 0
 
 
-def workload_config():
+def workload_config(storage="f32"):
     return {"workload": f"{GRID[0]}^3 Si/SiO2 eps map (seed 1), PEC walls, Jz dipole lambda=20 at the "
-                        f"centre, {STEPS_PER_CALL} steps per call, FP32 fields",
+                        f"centre, {STEPS_PER_CALL} steps per call, {storage.upper()} fields",
             "grid_xyz": list(GRID[::-1]), "steps_per_call": STEPS_PER_CALL,
             "l2": "inputs larger than L2 (470 MB device state), no flush",
             "parallelism": "replicas (one independent simulation per GPU)"}
+
+
+def time_storage_variant(shape, eps, J, src, storage, device, stream, n_calls=1):
+    """GCUPS of both schedules with 16-bit field storage on the same workload
+    (one warm-up call, then n_calls timed calls each)."""
+    from paper_2502_20610_gb300 import fdtd
+    from paper_2502_20610_gb300 import workloads as wl
+    cells = shape[0] * shape[1] * shape[2]
+    out = {"storage": storage, "unit": "GCUPS",
+           "stream_bytes_per_cell_step": 12.0 * STORAGE_BYTES[storage]}
+    for scheme in ("systolic", "naive"):
+        sim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme=scheme, device=device, storage=storage,
+                       steps_per_launch=STEPS_PER_CALL, max_source_steps=J.size)
+        sim.add_source(*src, J)
+        sim.step(STEPS_PER_CALL)
+        sim.sync()
+        t = time_calls(sim, n_calls, stream)
+        sim.sync()
+        sim.close()
+        out[scheme] = cells * STEPS_PER_CALL * n_calls / t / 1e9
+    peak, kind = load_peaks()
+    bound = peak / out["stream_bytes_per_cell_step"]
+    out["stream_bound_gcups"] = bound
+    out["systolic_stream_frac"] = out["systolic"] / bound
+    out["peak_kind"] = kind
+    return out
 
 
 def time_calls(sim, n_calls, stream):
@@ -242,6 +282,8 @@ def main():
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
     ap.add_argument("--scheme", default="systolic", choices=["systolic", "naive"])
     ap.add_argument("--tile", default=None, help="systolic tile shape, e.g. 31x15x15 (default: library's)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"], help="field storage format")
+    ap.add_argument("--no-16bit", action="store_true", help="skip the FP16/BF16 storage context lines")
     args = ap.parse_args()
     GRID = (args.grid,) * 3
     STEPS_PER_CALL = args.steps_per_call
@@ -261,7 +303,8 @@ def main():
     eps, J, (c, i, j, k) = make_workload(shape)
 
     sim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme=args.scheme, device=device,
-                   steps_per_launch=STEPS_PER_CALL, max_source_steps=J.size, tile=args.tile)
+                   steps_per_launch=STEPS_PER_CALL, max_source_steps=J.size, tile=args.tile,
+                   storage=args.storage)
     sim.add_source(c, i, j, k, J)
     for _ in range(args.warmup):
         sim.step(STEPS_PER_CALL)
@@ -282,7 +325,8 @@ def main():
     # naive schedule on the same workload (context for "systolic vs naive")
     naive = None
     if args.naive_calls > 0:
-        nsim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme="naive", device=device, max_source_steps=J.size)
+        nsim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme="naive", device=device, max_source_steps=J.size,
+                        storage=args.storage)
         nsim.add_source(c, i, j, k, J)
         nsim.step(STEPS_PER_CALL)
         nsim.sync()
@@ -291,7 +335,9 @@ def main():
         naive_gcups = cells * STEPS_PER_CALL * args.naive_calls / t / 1e9
         naive = {"value": naive_gcups, "unit": "GCUPS", "ms_per_step": 1e3 * t / args.naive_calls,
                  "kernels_per_step": 2 * STEPS_PER_CALL,
-                 "hbm_gbs_at_76B": naive_gcups * NAIVE_BYTES, "speedup_systolic": gcups / world / naive_gcups}
+                 "algorithmic_bytes_per_cell_step": naive_bytes(STORAGE_BYTES[args.storage]),
+                 "hbm_gbs_algorithmic": naive_gcups * naive_bytes(STORAGE_BYTES[args.storage]),
+                 "speedup_systolic": gcups / world / naive_gcups}
         nsim.close()
 
     # end to end through the public API with host buffers: H2D of the initial
@@ -300,7 +346,7 @@ def main():
     if not args.no_e2e:
         host_in = torch.from_numpy(wl.random_fields(shape, 0)).pin_memory()
         host_out = torch.empty((6,) + shape, dtype=torch.float32).pin_memory()
-        nb = 6 * cells * 4
+        nb = 6 * cells * 4  # the API exchanges FP32 fields whatever the storage
         sim.write_fields(host_in)
         sim.step(STEPS_PER_CALL)
         sim.read_fields(out=host_out)
@@ -316,30 +362,37 @@ def main():
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
     sim.close()
 
+    # the same workload with 16-bit field storage (FP32 arithmetic), both schedules
+    narrow = None
+    if not args.no_16bit and args.storage == "f32" and args.scheme == "systolic":
+        narrow = [time_storage_variant(shape, eps, J, (c, i, j, k), st, device, stream) for st in ("f16", "bf16")]
+
     if rank != 0:
         return 0
     peak, peak_kind = load_peaks()
     per_launch_s = elapsed / max(launches, 1)
     cell_steps_per_launch = cells * STEPS_PER_CALL * args.steps / max(launches, 1)
     tile = args.tile or DEFAULT_TILE
-    sys_bytes = systolic_bytes(tile) if args.scheme == "systolic" else NAIVE_BYTES
-    per_update = MEASURED_TRAFFIC.get(tile) if args.scheme == "systolic" else None
+    eb = STORAGE_BYTES[args.storage]
+    sys_bytes = systolic_bytes(tile, eb) if args.scheme == "systolic" else naive_bytes(eb)
+    per_update = MEASURED_TRAFFIC.get(tile) if args.scheme == "systolic" and args.storage == "f32" else None
     traffic = per_update * cell_steps_per_launch + 52.0 * cells if per_update else None
     achieved = sys_bytes * cell_steps_per_launch / per_launch_s / 1e9
     line = {
         "metric": "GCUPS of 3D Yee update, systolic vs naive kernel, FP32 & FP16-stored, 1 GB300",
         "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(),
-        "scheme": args.scheme,
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args.storage),
+        "scheme": args.scheme, "storage": args.storage,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "systolic_reg_kernel" if args.scheme == "systolic" else "naive_h/e",
                      "tile": tile, "algorithmic_bytes_per_cell_step": round(sys_bytes, 3)},
-        "stream_roofline": {"bytes_per_cell_step": STREAM_BYTES,
-                            "bound_gcups": peak / STREAM_BYTES,
-                            "frac": gcups / world / (peak / STREAM_BYTES), "peak_kind": peak_kind},
+        "stream_roofline": {"bytes_per_cell_step": 12.0 * eb,
+                            "bound_gcups": peak / (12.0 * eb),
+                            "frac": gcups / world / (peak / (12.0 * eb)), "peak_kind": peak_kind},
         "naive": naive,
+        "storage_16bit": narrow,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,

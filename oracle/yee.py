@@ -46,8 +46,25 @@ def _load():
     lib.oracle_energy.restype = ctypes.c_double
     lib.oracle_energy.argtypes = [P]
     lib.oracle_div.argtypes = [P, D, D]
+    lib.oracle_round_to_format.restype = ctypes.c_double
+    lib.oracle_round_to_format.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.oracle_set_storage.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, D]
     _lib = lib
     return lib
+
+
+#: 16-bit storage formats: (significant bits p, emin, emax)
+FORMATS = {"f16": (11, -14, 15), "bf16": (8, -126, 127)}
+
+
+def round_to_format(x, fmt):
+    """Elementwise nearest value of the 16-bit format `fmt` (ties to even),
+    computed by the oracle's own rounding routine; returns float64."""
+    lib = _load()
+    p, emin, emax = FORMATS[fmt]
+    x = np.asarray(x, dtype=np.float64)
+    f = lib.oracle_round_to_format
+    return np.array([f(float(v), p, emin, emax) for v in x.ravel()], dtype=np.float64).reshape(x.shape)
 
 
 def _dptr(a):
@@ -131,6 +148,17 @@ class YeeOracle:
         Hy term, 2 wrong difference axis in Hz, 3 wrong difference axis in Ex,
         4 half the H time step, 5 source sign."""
         self._lib.oracle_set_mutation(self._h, int(m))
+
+    def set_storage(self, fmt, scales=None):
+        """Round stored fields to the 16-bit format `fmt` ("f16", "bf16") from
+        now on, as s_c * R(v / s_c) (scales: six powers of two, default 1);
+        None switches rounding off.  The current fields are rounded at once."""
+        sc = np.ascontiguousarray(np.ones(6) if scales is None else np.asarray(scales, dtype=np.float64))
+        if fmt is None:
+            self._lib.oracle_set_storage(self._h, 0, 0, 0, _dptr(sc))
+        else:
+            p, emin, emax = FORMATS[fmt]
+            self._lib.oracle_set_storage(self._h, p, emin, emax, _dptr(sc))
 
     def energy(self):
         return float(self._lib.oracle_energy(self._h))

@@ -25,10 +25,18 @@
  *   (i=0: Ey,Ez; j=0: Ex,Ez; k=0: Ex,Ey) is never updated.
  *   PERIODIC: every index wraps (oracle-only; used for the dispersion pin).
  *
+ * 16-bit field storage (the FP16 / BF16 storage option of the GPU library):
+ *   when switched on, every value of field c is kept as s_c * R(v / s_c)
+ *   with a power-of-two scale s_c, R rounding to the nearest number of the
+ *   16-bit format (ties to even): H values right after the H half-step, E
+ *   values after the E half-step and the point sources.  Arithmetic stays
+ *   FP64; only what is stored is rounded.
+ *
  * Pins (see tests/test_oracle_pins.py): exact energy invariant, Gauss-law
  * invariants, closed-form discrete cavity eigenmodes, the Yee dispersion
  * relation for periodic plane waves, the source work identity and planted
- * mutations that each of those must catch.
+ * mutations that each of those must catch; the storage rounding against
+ * numpy's binary16 and torch's bfloat16 conversions.
  */
 #include <math.h>
 #include <stdint.h>
@@ -53,6 +61,8 @@ typedef struct {
     int nsrc;
     or_source src[OR_MAX_SOURCES];
     int mutation;  /* 0 = none; >0 plants a known mistake (pin sensitivity tests) */
+    int sp, semin, semax;  /* storage rounding: significant bits (0 = off), exponent range */
+    double sscale[6];
 } yee_oracle;
 
 static long ncell(const yee_oracle *o) { return (long)o->nx * o->ny * o->nz; }
@@ -103,6 +113,45 @@ void oracle_get_field(const yee_oracle *o, int comp, double *dst)
 void oracle_get_ce(const yee_oracle *o, double *dst)
 {
     memcpy(dst, o->ce, sizeof(double) * (size_t)ncell(o));
+}
+
+/* Round x to the nearest number with p significant bits whose exponent is
+ * at least emin (below 2^emin the spacing stays 2^(emin-p+1): subnormals),
+ * ties to even; results of magnitude >= 2^(emax+1) become infinite.
+ * IEEE binary16: p = 11, emin = -14, emax = 15.  bfloat16: p = 8,
+ * emin = -126, emax = 127.  Scaling by powers of two is exact in FP64 here. */
+double oracle_round_to_format(double x, int p, int emin, int emax)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    frexp(x, &e); /* |x| in [2^(e-1), 2^e) */
+    int lead = e - 1;
+    if (lead < emin) lead = emin;
+    double ulp = ldexp(1.0, lead - (p - 1));
+    double r = nearbyint(x / ulp) * ulp; /* default rounding mode: ties to even */
+    if (fabs(r) >= ldexp(1.0, emax + 1)) r = copysign(INFINITY, x);
+    return r;
+}
+
+static void round_field(yee_oracle *o, int c)
+{
+    if (o->sp <= 0) return;
+    long n = ncell(o);
+    double s = o->sscale[c];
+    for (long q = 0; q < n; ++q) o->f[c][q] = s * oracle_round_to_format(o->f[c][q] / s, o->sp, o->semin, o->semax);
+}
+
+/* Switch 16-bit storage rounding on (p > 0) or off (p = 0) with per-component
+ * power-of-two scales; the current fields are rounded at once. */
+void oracle_set_storage(yee_oracle *o, int p, int emin, int emax, const double *scale)
+{
+    o->sp = p;
+    o->semin = emin;
+    o->semax = emax;
+    for (int c = 0; c < 6; ++c) {
+        o->sscale[c] = scale ? scale[c] : 1.0;
+        round_field(o, c);
+    }
 }
 
 long oracle_current_step(const yee_oracle *o) { return o->step; }
@@ -213,6 +262,7 @@ int oracle_step(yee_oracle *o, long n)
     for (long s = 0; s < n; ++s) {
         half_step_h(o, tmp);
         for (int a = 0; a < 3; ++a) { double *t = o->f[HX + a]; o->f[HX + a] = tmp[a]; tmp[a] = t; }
+        for (int a = 0; a < 3; ++a) round_field(o, HX + a);
         half_step_e(o, tmp);
         for (int a = 0; a < 3; ++a) { double *t = o->f[EX + a]; o->f[EX + a] = tmp[a]; tmp[a] = t; }
         for (int q = 0; q < o->nsrc; ++q) {
@@ -221,6 +271,7 @@ int oracle_step(yee_oracle *o, long n)
             double sign = (o->mutation == 5) ? 1.0 : -1.0;
             o->f[src->comp][src->idx] += sign * o->ce[src->idx] * J;
         }
+        for (int a = 0; a < 3; ++a) round_field(o, EX + a);
         o->step += 1;
     }
     for (int a = 0; a < 3; ++a) free(tmp[a]);

@@ -23,8 +23,9 @@ constexpr unsigned EPOCH_LIMIT = 1u << 30;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t fields[6], ce, src, progress, tiles, ctrl, total;
-    int pitch;  // floats per x row in device memory (nx rounded up to 16 bytes)
+    size_t fields[6], ce, stage, src, progress, tiles, ctrl, total;
+    int eb;     // bytes per stored field value (4 FP32, 2 FP16/BF16)
+    int pitch;  // elements per x row in device memory (nx rounded up to 16 bytes)
     int variant, tx, ty, tz;  // systolic tile shape
     int gx, gy, gz;
     long long ntiles_max;
@@ -47,21 +48,26 @@ int pick_variant(const fdtd_coeffs &c)
 }
 
 // Everything lives in the caller's workspace:
-//   6 FP32 field arrays, the FP32 coefficient dt/eps, the source tables,
+//   6 field arrays in the storage format, the FP32 coefficient dt/eps, (16-bit
+//   storage) one dense FP32 component for host transfers, the source tables,
 //   and (systolic) one progress flag per skewed tile plus the tile order.
 bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, Layout &L)
 {
     // rows padded to a 16-byte multiple, so every row starts 16-byte aligned
     // (a requirement of bulk tensor copies); the padding cells are never read
-    L.pitch = (g.nx + 3) / 4 * 4;
+    L.eb = storage_bytes(c.storage);
+    const int q = 16 / L.eb;
+    L.pitch = (g.nx + q - 1) / q * q;
     const long long n = (long long)L.pitch * g.ny * g.nz;
     size_t off = 0;
     for (int k = 0; k < 6; ++k) {
         L.fields[k] = off;
-        off = align_up(off + sizeof(float) * (size_t)n);
+        off = align_up(off + (size_t)L.eb * (size_t)n);
     }
     L.ce = off;
     off = align_up(off + sizeof(float) * (size_t)n);
+    L.stage = off;
+    if (c.storage != FDTD_STORAGE_F32) off = align_up(off + sizeof(float) * (size_t)g.nx * g.ny * g.nz);
     L.source_steps = c.max_source_steps > 0 ? c.max_source_steps : DEFAULT_SOURCE_STEPS;
     L.src = off;
     off = align_up(off + sizeof(float) * (size_t)FDTD_MAX_SOURCES * (size_t)L.source_steps);
@@ -100,11 +106,22 @@ fdtd_status check_args(const fdtd_grid *g, const fdtd_coeffs *c, const fdtd_boun
     if (!(c->dt > 0.0) || !std::isfinite(c->dt)) return FDTD_ERR_INVALID_ARG;
     if (c->scheme != FDTD_SCHEME_NAIVE && c->scheme != FDTD_SCHEME_SYSTOLIC) return FDTD_ERR_INVALID_ARG;
     if (c->storage < FDTD_STORAGE_F32 || c->storage > FDTD_STORAGE_BF16) return FDTD_ERR_INVALID_ARG;
-    if (c->storage != FDTD_STORAGE_F32) return FDTD_ERR_UNSUPPORTED;
+    if (c->storage != FDTD_STORAGE_F32) {
+        for (int a = 0; a < 6; ++a) {
+            const float s = c->field_scale[a];
+            int ex = 0;
+            if (s == 0.f) continue;  // 0 = 1
+            if (!(s > 0.f) || !std::isfinite(s) || std::frexp(s, &ex) != 0.5f) return FDTD_ERR_INVALID_ARG;
+            if (ex < -100 || ex > 100) return FDTD_ERR_INVALID_ARG;
+        }
+    }
     for (int a = 0; a < 3; ++a) {
         if (c->tile[a] < 0 || c->cluster[a] < 0) return FDTD_ERR_INVALID_ARG;
     }
     if (pick_variant(*c) < 0) return FDTD_ERR_UNSUPPORTED;
+    // the shared-memory systolic kernels (tiles 31x15x15, 31x7x15) hold FP32 only
+    if (c->scheme == FDTD_SCHEME_SYSTOLIC && c->storage != FDTD_STORAGE_F32 && pick_variant(*c) < 2)
+        return FDTD_ERR_UNSUPPORTED;
     for (int a = 0; a < 3; ++a)
         if (c->cluster[a] > 1) return FDTD_ERR_UNSUPPORTED;
     if (b->kind < FDTD_BOUNDARY_PEC || b->kind > FDTD_BOUNDARY_LEARNED) return FDTD_ERR_INVALID_ARG;
@@ -187,23 +204,29 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-bool encode_shell_maps(CUtensorMap tm[3][7], float *fbase, long long fstride, int nx, int ny, int nz,
-                       int pitch, int nr)
+bool encode_shell_maps(CUtensorMap tm[3][7], void *fbase, long long fstride, const float *ce, int storage,
+                       int nx, int ny, int nz, int pitch, int nr)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || fstride <= 0) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4u, (cuuint64_t)pitch * (cuuint64_t)ny * 4u};
-    // lower z shell {36,16,1}, lower y shell {36,1,nr}, lower x shell {4,16,nr}
-    const cuuint32_t box[3][3] = {{36, 16, 1}, {36, 1, (cuuint32_t)nr}, {4, 16, (cuuint32_t)nr}};
     const cuuint32_t estr[3] = {1, 1, 1};
-    for (int s = 0; s < 3; ++s)
-        for (int a = 0; a < 7; ++a) {
-            CUresult r = enc(&tm[s][a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, fbase + a * fstride, dims, strides,
-                             box[s], estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    for (int a = 0; a < 7; ++a) {
+        // array 6 is dt/eps (FP32); the fields use the storage element
+        const int eb = a < 6 ? storage_bytes(storage) : 4;
+        const cuuint32_t xa = 16u / (cuuint32_t)eb, sw = 32u + xa;
+        const cuuint64_t strides[2] = {(cuuint64_t)pitch * eb, (cuuint64_t)pitch * (cuuint64_t)ny * eb};
+        // lower z shell {sw,16,1}, lower y shell {sw,1,nr}, lower x shell {xa,16,nr}
+        const cuuint32_t box[3][3] = {{sw, 16, 1}, {sw, 1, (cuuint32_t)nr}, {xa, 16, (cuuint32_t)nr}};
+        void *base = a < 6 ? (void *)((char *)fbase + (size_t)a * (size_t)fstride * eb) : (void *)ce;
+        const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+        for (int s = 0; s < 3; ++s) {
+            CUresult r = enc(&tm[s][a], dt, 3, base, dims, strides, box[s], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return false;
         }
+    }
     return true;
 }
 
@@ -236,8 +259,10 @@ struct fdtd_sim {
     cudaStream_t stream;
     char *ws;
     Layout L;
-    float *f[6];
+    void *f[6];
     float *ce;
+    float *stage;  // dense FP32 component (16-bit storage), else null
+    Scales sc;
     float *src_tab;
     unsigned *progress;
     int *tiles;
@@ -274,6 +299,17 @@ cudaError_t copy_rows(float *dst, size_t dpitch, const float *src, size_t spitch
         return cudaMemcpyAsync(dst, src, w * rows, cudaMemcpyDefault, st);
     return cudaMemcpy2DAsync(dst, sizeof(float) * dpitch, src, sizeof(float) * spitch, w, rows,
                              cudaMemcpyDefault, st);
+}
+
+// True if `p` is device (or managed) memory the kernels can read and write.
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // pageable host memory on older runtimes
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 #define CK(x)                                                                  \
@@ -333,8 +369,15 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     h->stream = (cudaStream_t)stream;
     h->ws = (char *)d_workspace;
     h->L = L;
-    for (int k = 0; k < 6; ++k) h->f[k] = (float *)(h->ws + L.fields[k]);
+    for (int k = 0; k < 6; ++k) h->f[k] = h->ws + L.fields[k];
     h->ce = (float *)(h->ws + L.ce);
+    h->stage = coeffs->storage != FDTD_STORAGE_F32 ? (float *)(h->ws + L.stage) : nullptr;
+    for (int k = 0; k < 6; ++k) {
+        const float sk = coeffs->storage != FDTD_STORAGE_F32 && coeffs->field_scale[k] != 0.f ? coeffs->field_scale[k]
+                                                                                             : 1.f;
+        h->sc.s[k] = sk;
+        h->sc.is[k] = 1.f / sk;  // exact: sk is a power of two
+    }
     h->src_tab = (float *)(h->ws + L.src);
     h->progress = (unsigned *)(h->ws + L.progress);
     h->tiles = (int *)(h->ws + L.tiles);
@@ -361,8 +404,8 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
         e = cudaMemcpy2DAsync(h->ce, sizeof(float) * L.pitch, ce.data(), sizeof(float) * grid->nx,
                               sizeof(float) * grid->nx, (size_t)grid->ny * grid->nz, cudaMemcpyHostToDevice,
                               h->stream);
-    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
-        e = cudaMemsetAsync(h->f[k], 0, sizeof(float) * padded, h->stream);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)  // all-zero bits are +0 in every format
+        e = cudaMemsetAsync(h->f[k], 0, (size_t)L.eb * padded, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ctrl, 0, 64 * sizeof(int), h->stream);
     if (e == cudaSuccess && L.ntiles_max > 0)
         e = cudaMemsetAsync(h->progress, 0, sizeof(unsigned) * (size_t)L.ntiles_max, h->stream);
@@ -370,19 +413,19 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     if (e != cudaSuccess) return fail(cuda_status(e));
 
     if (coeffs->scheme == FDTD_SCHEME_SYSTOLIC) {
-        e = systolic_configure(L.variant);
+        e = systolic_configure(L.variant, coeffs->storage);
         if (e != cudaSuccess) return fail(cuda_status(e));
         int dev = 0, sms = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return fail(cuda_status(e));
-        const int per_sm = systolic_max_ctas_per_sm(L.variant);
+        const int per_sm = systolic_max_ctas_per_sm(L.variant, coeffs->storage);
         if (per_sm < 1) return fail(FDTD_ERR_UNSUPPORTED);
         h->max_ctas = sms * per_sm;
         if (L.variant >= 2) {
-            const long long fstride = (long long)(L.fields[1] - L.fields[0]) / (long long)sizeof(float);
-            if (!encode_shell_maps(h->tm, h->f[0], fstride, grid->nx, grid->ny, grid->nz, L.pitch,
-                                   systolic_reg_rows(L.variant - 2)))
+            const long long fstride = (long long)(L.fields[1] - L.fields[0]) / L.eb;
+            if (!encode_shell_maps(h->tm, h->f[0], fstride, h->ce, coeffs->storage, grid->nx, grid->ny, grid->nz,
+                                   L.pitch, systolic_reg_rows(L.variant - 2)))
                 return fail(FDTD_ERR_UNSUPPORTED);
         }
         fdtd_status st = upload_tiles(h, 0, 0);
@@ -427,8 +470,21 @@ fdtd_status fdtd_write_fields(fdtd_handle h, const float *src)
 {
     if (!h || !src) return FDTD_ERR_INVALID_ARG;
     const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
-    for (int k = 0; k < 6; ++k)
-        CK(copy_rows(h->f[k], h->L.pitch, src + (size_t)k * n, h->g.nx, h->g, h->stream));
+    if (h->c.storage == FDTD_STORAGE_F32) {
+        for (int k = 0; k < 6; ++k)
+            CK(copy_rows((float *)h->f[k], h->L.pitch, src + (size_t)k * n, h->g.nx, h->g, h->stream));
+    } else {
+        const bool dev = is_device_pointer(src);
+        for (int k = 0; k < 6; ++k) {
+            const float *from = src + (size_t)k * n;
+            if (!dev) {  // through the dense FP32 stage
+                CK(cudaMemcpyAsync(h->stage, from, sizeof(float) * n, cudaMemcpyDefault, h->stream));
+                from = h->stage;
+            }
+            CK(launch_to_storage(h->f[k], from, h->c.storage, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->sc.is[k],
+                                 h->stream));
+        }
+    }
     CK(cudaMemsetAsync(h->ctrl + 1, 0, 3 * sizeof(int), h->stream));
     h->failed = false;
     return FDTD_OK;
@@ -441,9 +497,9 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
     if (h->c.scheme == FDTD_SCHEME_NAIVE) {
         const float ndt = -(float)h->c.dt;
         for (int64_t s = 0; s < n; ++s) {
-            CK(launch_naive_h(h->f, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->stream));
-            CK(launch_naive_e(h->f, h->ce, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->step, h->src,
-                              h->stream));
+            CK(launch_naive_h(h->f, h->c.storage, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->sc, h->stream));
+            CK(launch_naive_e(h->f, h->c.storage, h->ce, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->step, h->src,
+                              h->sc, h->stream));
             h->launches += 2;
             h->step += 1;
         }
@@ -457,14 +513,15 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         }
         CK(cudaMemsetAsync(h->ctrl, 0, sizeof(int), h->stream));  // ticket counter
         SysLaunch p;
-        for (int k = 0; k < 6; ++k) p.f[k] = h->f[k];
+        for (int k = 0; k < 6; ++k) p.f[k] = (float *)h->f[k];
         p.ce = h->ce;
         p.nx = h->g.nx;
         p.ny = h->g.ny;
         p.nz = h->g.nz;
         p.pitch = h->L.pitch;
-        p.fbase = h->f[0];
-        p.fstride = (long long)(h->L.fields[1] - h->L.fields[0]) / (long long)sizeof(float);
+        p.fbase = (float *)h->f[0];
+        p.fstride = (long long)(h->L.fields[1] - h->L.fields[0]) / h->L.eb;
+        p.sc = h->sc;
         p.gx = h->L.gx;
         p.gy = h->L.gy;
         p.gz = h->L.gz;
@@ -485,7 +542,7 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         p.src = h->src;
         if (h->L.variant >= 2) std::memcpy(p.tm, h->tm, sizeof(p.tm));
         const int grid = (int)std::max<long long>(1, std::min<long long>(p.ntiles, h->max_ctas));
-        CK(launch_systolic(p, grid, h->stream, h->L.variant));
+        CK(launch_systolic(p, grid, h->stream, h->L.variant, h->c.storage));
         h->launches += 1;
         h->epoch += (unsigned)T + 1u;
         h->step += T;
@@ -513,10 +570,18 @@ fdtd_status fdtd_read_fields(fdtd_handle h, uint32_t component_mask, float *dst)
     fdtd_status s = fdtd_sync(h);
     if (s != FDTD_OK) return s;
     const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+    const bool dev = h->c.storage == FDTD_STORAGE_F32 || is_device_pointer(dst);
     size_t q = 0;
     for (int k = 0; k < 6; ++k) {
         if (!(component_mask & (1u << k))) continue;
-        CK(copy_rows(dst + q * n, h->g.nx, h->f[k], h->L.pitch, h->g, h->stream));
+        if (h->c.storage == FDTD_STORAGE_F32) {
+            CK(copy_rows(dst + q * n, h->g.nx, (const float *)h->f[k], h->L.pitch, h->g, h->stream));
+        } else {
+            float *to = dev ? dst + q * n : h->stage;
+            CK(launch_from_storage(to, h->f[k], h->c.storage, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->sc.s[k],
+                                   h->stream));
+            if (!dev) CK(cudaMemcpyAsync(dst + q * n, h->stage, sizeof(float) * n, cudaMemcpyDefault, h->stream));
+        }
         ++q;
     }
     CK(cudaStreamSynchronize(h->stream));

@@ -4,9 +4,11 @@
 #include <cstdint>
 #include <cuda.h>  // CUtensorMap (type only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <vector>
 
 #include "fdtd.h"
+#include "storage.cuh"
 
 #define FDTD_MAX_SOURCES 16
 
@@ -28,11 +30,19 @@ struct SrcSet {
 };
 
 // Naive scheme: one H launch and one E launch per step.
-// Arrays are nx*ny*nz cells with rows of `pitch` floats (pitch >= nx).
-cudaError_t launch_naive_h(float *const f[6], int nx, int ny, int nz, int pitch, float neg_dt,
-                           cudaStream_t st);
-cudaError_t launch_naive_e(float *const f[6], const float *ce, int nx, int ny, int nz, int pitch,
-                           long long step, const SrcSet &src, cudaStream_t st);
+// Arrays are nx*ny*nz cells with rows of `pitch` elements (pitch >= nx) of
+// the storage format `storage` (FDTD_STORAGE_*); dt/eps is always FP32.
+cudaError_t launch_naive_h(void *const f[6], int storage, int nx, int ny, int nz, int pitch, float neg_dt,
+                           const Scales &sc, cudaStream_t st);
+cudaError_t launch_naive_e(void *const f[6], int storage, const float *ce, int nx, int ny, int nz, int pitch,
+                           long long step, const SrcSet &src, const Scales &sc, cudaStream_t st);
+
+// FP32 <-> storage conversion of one component (convert.cu): `dense` holds
+// nx*ny*nz values, `pitched` rows of `pitch` elements.
+cudaError_t launch_to_storage(void *pitched, const float *dense, int storage, int nx, int ny, int nz, int pitch,
+                              float inv_scale, cudaStream_t st);
+cudaError_t launch_from_storage(float *dense, const void *pitched, int storage, int nx, int ny, int nz,
+                                int pitch, float scale, cudaStream_t st);
 
 // Systolic scheme: the subdomain ("tile") geometry is a compile-time ring of
 // 32 x RY x RZ shared-memory slots per CTA of which 31 x (RY-1) x (RZ-1)
@@ -43,16 +53,18 @@ struct SysShape { int tx, ty, tz; };
 constexpr int SYS_NSHAPES = 4;  // 2, 3: register-resident kernel, 31 x 15 x 12 / x 8 (systolic_reg.cu)
 SysShape systolic_shape(int variant);
 SysShape systolic_reg_shape(int k);
-cudaError_t systolic_reg_configure(int k);
-int systolic_reg_max_ctas_per_sm(int k);
+cudaError_t systolic_reg_configure(int k, int storage);
+int systolic_reg_max_ctas_per_sm(int k, int storage);
 
 struct SysLaunch {
-    float *f[6];
+    float *f[6];             // field arrays (elements of the storage format; FP32 for the
+                             // shared-memory kernel)
     const float *ce;
     int nx, ny, nz;
-    int pitch;               // floats between consecutive x rows (>= nx)
-    float *fbase;            // f[c] == fbase + c*fstride for c in 0..5 and ce == fbase + 6*fstride,
-    long long fstride;       // when the arrays sit at a uniform stride (else fstride == 0)
+    int pitch;               // elements between consecutive x rows (>= nx)
+    float *fbase;            // f[c] == fbase + c*fstride elements for c in 0..5 when the
+    long long fstride;       // arrays sit at a uniform stride (else fstride == 0)
+    Scales sc;               // storage scales (16-bit formats)
     int gx, gy, gz;          // tile grid over skewed space sigma = p + t
     int T;                   // steps of this launch
     unsigned epoch;          // progress values of this launch are epoch + k
@@ -72,16 +84,19 @@ struct SysLaunch {
 };
 
 // Encode the 21 shell maps of the register kernel with `nr` z rows per
-// column; fbase/fstride/pitch as in SysLaunch.  Returns false on failure.
-bool encode_shell_maps(CUtensorMap tm[3][7], float *fbase, long long fstride, int nx, int ny, int nz,
-                       int pitch, int nr);
+// column: the six fields (storage format `storage`, at fbase + c*fstride
+// elements) and the FP32 coefficient array ce, all with rows of `pitch`
+// elements.  Returns false on failure.
+bool encode_shell_maps(CUtensorMap tm[3][7], void *fbase, long long fstride, const float *ce, int storage,
+                       int nx, int ny, int nz, int pitch, int nr);
 int systolic_reg_rows(int k);
 
 size_t systolic_smem_bytes(int variant);
-cudaError_t systolic_configure(int variant);
-int systolic_max_ctas_per_sm(int variant);
-cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant);
-cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k);
+cudaError_t systolic_configure(int variant, int storage);
+int systolic_max_ctas_per_sm(int variant, int storage);
+// The shared-memory variants (0, 1) take FP32 storage only.
+cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant, int storage);
+cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int storage);
 
 // Tile order for one systolic launch of up to T steps (fdtd_api.cu).
 void systolic_tile_order(const fdtd_grid &g, int variant, int T, std::vector<int> &tiles,

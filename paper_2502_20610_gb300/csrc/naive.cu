@@ -7,18 +7,22 @@
 // Layout: 256-thread CTAs of 32 (x) x 8 (y) threads; each thread marches up
 // a column of NAIVE_KZ cells in z and carries the z-neighbour in registers,
 // so x rows are read coalesced and the z-neighbour plane is read once.
+// Fields are stored as FP32, FP16 or BF16 (storage.cuh); arithmetic is FP32.
 #include "internal.h"
+#include "storage.cuh"
 #include "yee_cell.cuh"
 
 namespace {
 
 constexpr int NAIVE_BX = 32, NAIVE_BY = 8, NAIVE_KZ = 8;
 
+template <class S>
 __global__ void __launch_bounds__(NAIVE_BX *NAIVE_BY)
-naive_h_kernel(float *__restrict__ ex_, float *__restrict__ ey_, float *__restrict__ ez_,
-               float *__restrict__ hx_, float *__restrict__ hy_, float *__restrict__ hz_,
-               int nx, int ny, int nz, int pitch, float ndt)
+naive_h_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ ey_, typename S::T *__restrict__ ez_,
+               typename S::T *__restrict__ hx_, typename S::T *__restrict__ hy_, typename S::T *__restrict__ hz_,
+               int nx, int ny, int nz, int pitch, float ndt, const Scales sc)
 {
+    using T = typename S::T;
     const int i = blockIdx.x * NAIVE_BX + threadIdx.x;
     const int j = blockIdx.y * NAIVE_BY + threadIdx.y;
     const int k0 = blockIdx.z * NAIVE_KZ;
@@ -26,50 +30,55 @@ naive_h_kernel(float *__restrict__ ex_, float *__restrict__ ey_, float *__restri
     const int k1 = min(k0 + NAIVE_KZ, nz);
     const long long sxy = (long long)pitch * ny;
     const bool ip = i + 1 < nx, jp = j + 1 < ny;
-    const float *Ex = ex_, *Ey = ey_, *Ez = ez_;
+    const T *Ex = ex_, *Ey = ey_, *Ez = ez_;
+    const float s0 = sc.s[0], s1 = sc.s[1], s2 = sc.s[2];
     long long p = i + (long long)pitch * (j + (long long)ny * k0);
-    float exc = __ldg(Ex + p), eyc = __ldg(Ey + p);
+    float exc = S::dec(__ldg(Ex + p), s0), eyc = S::dec(__ldg(Ey + p), s1);
     for (int k = k0; k < k1; ++k, p += sxy) {
         const bool kp = k + 1 < nz;
-        const float exn = kp ? __ldg(Ex + p + sxy) : 0.f;
-        const float eyn = kp ? __ldg(Ey + p + sxy) : 0.f;
-        const float ez = __ldg(Ez + p);
-        const float ez_ip = ip ? __ldg(Ez + p + 1) : 0.f;
-        const float ey_ip = ip ? __ldg(Ey + p + 1) : 0.f;
-        const float ez_jp = jp ? __ldg(Ez + p + pitch) : 0.f;
-        const float ex_jp = jp ? __ldg(Ex + p + pitch) : 0.f;
-        hx_[p] = h_x(hx_[p], ez_jp, ez, eyn, eyc, ndt);
-        hy_[p] = h_y(hy_[p], exn, exc, ez_ip, ez, ndt);
-        hz_[p] = h_z(hz_[p], ey_ip, eyc, ex_jp, exc, ndt);
+        const float exn = kp ? S::dec(__ldg(Ex + p + sxy), s0) : 0.f;
+        const float eyn = kp ? S::dec(__ldg(Ey + p + sxy), s1) : 0.f;
+        const float ez = S::dec(__ldg(Ez + p), s2);
+        const float ez_ip = ip ? S::dec(__ldg(Ez + p + 1), s2) : 0.f;
+        const float ey_ip = ip ? S::dec(__ldg(Ey + p + 1), s1) : 0.f;
+        const float ez_jp = jp ? S::dec(__ldg(Ez + p + pitch), s2) : 0.f;
+        const float ex_jp = jp ? S::dec(__ldg(Ex + p + pitch), s0) : 0.f;
+        hx_[p] = S::enc(h_x(S::dec(hx_[p], sc.s[3]), ez_jp, ez, eyn, eyc, ndt), sc.is[3]);
+        hy_[p] = S::enc(h_y(S::dec(hy_[p], sc.s[4]), exn, exc, ez_ip, ez, ndt), sc.is[4]);
+        hz_[p] = S::enc(h_z(S::dec(hz_[p], sc.s[5]), ey_ip, eyc, ex_jp, exc, ndt), sc.is[5]);
         exc = exn;
         eyc = eyn;
     }
 }
 
+template <class S>
 __global__ void __launch_bounds__(NAIVE_BX *NAIVE_BY)
-naive_e_kernel(float *__restrict__ ex_, float *__restrict__ ey_, float *__restrict__ ez_,
-               float *__restrict__ hx_, float *__restrict__ hy_, float *__restrict__ hz_,
+naive_e_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ ey_, typename S::T *__restrict__ ez_,
+               typename S::T *__restrict__ hx_, typename S::T *__restrict__ hy_, typename S::T *__restrict__ hz_,
                const float *__restrict__ ce_, int nx, int ny, int nz, int pitch, long long step,
-               const SrcSet src)
+               const SrcSet src, const Scales sc)
 {
+    using T = typename S::T;
     const int i = blockIdx.x * NAIVE_BX + threadIdx.x;
     const int j = blockIdx.y * NAIVE_BY + threadIdx.y;
     const int k0 = blockIdx.z * NAIVE_KZ;
     if (i >= nx || j >= ny || k0 >= nz) return;
     const int k1 = min(k0 + NAIVE_KZ, nz);
     const long long sxy = (long long)pitch * ny;
-    const float *Hx = hx_, *Hy = hy_, *Hz = hz_;
+    const T *Hx = hx_, *Hy = hy_, *Hz = hz_;
+    const float s3 = sc.s[3], s4 = sc.s[4], s5 = sc.s[5];
     long long p = i + (long long)pitch * (j + (long long)ny * k0);
-    float hxm = k0 > 0 ? __ldg(Hx + p - sxy) : 0.f;
-    float hym = k0 > 0 ? __ldg(Hy + p - sxy) : 0.f;
+    float hxm = k0 > 0 ? S::dec(__ldg(Hx + p - sxy), s3) : 0.f;
+    float hym = k0 > 0 ? S::dec(__ldg(Hy + p - sxy), s4) : 0.f;
     for (int k = k0; k < k1; ++k, p += sxy) {
-        const float hx = __ldg(Hx + p), hy = __ldg(Hy + p), hz = __ldg(Hz + p);
+        const float hx = S::dec(__ldg(Hx + p), s3), hy = S::dec(__ldg(Hy + p), s4);
+        const float hz = S::dec(__ldg(Hz + p), s5);
         const float ce = __ldg(ce_ + p);
-        float ex = ex_[p], ey = ey_[p], ez = ez_[p];
+        float ex = S::dec(ex_[p], sc.s[0]), ey = S::dec(ey_[p], sc.s[1]), ez = S::dec(ez_[p], sc.s[2]);
         // PEC: tangential E on the low planes is never updated
-        if (j > 0 && k > 0) ex = e_x(ex, hz, __ldg(Hz + p - pitch), hy, hym, ce);
-        if (i > 0 && k > 0) ey = e_y(ey, hx, hxm, hz, __ldg(Hz + p - 1), ce);
-        if (i > 0 && j > 0) ez = e_z(ez, hy, __ldg(Hy + p - 1), hx, __ldg(Hx + p - pitch), ce);
+        if (j > 0 && k > 0) ex = e_x(ex, hz, S::dec(__ldg(Hz + p - pitch), s5), hy, hym, ce);
+        if (i > 0 && k > 0) ey = e_y(ey, hx, hxm, hz, S::dec(__ldg(Hz + p - 1), s5), ce);
+        if (i > 0 && j > 0) ez = e_z(ez, hy, S::dec(__ldg(Hy + p - 1), s4), hx, S::dec(__ldg(Hx + p - pitch), s3), ce);
         for (int q = 0; q < src.n; ++q) {
             const SrcDesc &s = src.s[q];
             if (s.idx == p && step < s.n_amp) {
@@ -79,9 +88,9 @@ naive_e_kernel(float *__restrict__ ex_, float *__restrict__ ey_, float *__restri
                 else ez = add_source(ez, a);
             }
         }
-        ex_[p] = ex;
-        ey_[p] = ey;
-        ez_[p] = ez;
+        ex_[p] = S::enc(ex, sc.is[0]);
+        ey_[p] = S::enc(ey, sc.is[1]);
+        ez_[p] = S::enc(ez, sc.is[2]);
         hxm = hx;
         hym = hy;
     }
@@ -93,20 +102,40 @@ dim3 naive_grid(int nx, int ny, int nz)
                 (nz + NAIVE_KZ - 1) / NAIVE_KZ);
 }
 
-} // namespace
-
-cudaError_t launch_naive_h(float *const f[6], int nx, int ny, int nz, int pitch, float neg_dt,
-                           cudaStream_t st)
+template <class S>
+cudaError_t launch_h(void *const f[6], int nx, int ny, int nz, int pitch, float neg_dt, const Scales &sc,
+                     cudaStream_t st)
 {
-    naive_h_kernel<<<naive_grid(nx, ny, nz), dim3(NAIVE_BX, NAIVE_BY), 0, st>>>(
-        f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, pitch, neg_dt);
+    using T = typename S::T;
+    naive_h_kernel<S><<<naive_grid(nx, ny, nz), dim3(NAIVE_BX, NAIVE_BY), 0, st>>>(
+        (T *)f[0], (T *)f[1], (T *)f[2], (T *)f[3], (T *)f[4], (T *)f[5], nx, ny, nz, pitch, neg_dt, sc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_naive_e(float *const f[6], const float *ce, int nx, int ny, int nz, int pitch,
-                           long long step, const SrcSet &src, cudaStream_t st)
+template <class S>
+cudaError_t launch_e(void *const f[6], const float *ce, int nx, int ny, int nz, int pitch, long long step,
+                     const SrcSet &src, const Scales &sc, cudaStream_t st)
 {
-    naive_e_kernel<<<naive_grid(nx, ny, nz), dim3(NAIVE_BX, NAIVE_BY), 0, st>>>(
-        f[0], f[1], f[2], f[3], f[4], f[5], ce, nx, ny, nz, pitch, step, src);
+    using T = typename S::T;
+    naive_e_kernel<S><<<naive_grid(nx, ny, nz), dim3(NAIVE_BX, NAIVE_BY), 0, st>>>(
+        (T *)f[0], (T *)f[1], (T *)f[2], (T *)f[3], (T *)f[4], (T *)f[5], ce, nx, ny, nz, pitch, step, src, sc);
     return cudaGetLastError();
+}
+
+} // namespace
+
+cudaError_t launch_naive_h(void *const f[6], int storage, int nx, int ny, int nz, int pitch, float neg_dt,
+                           const Scales &sc, cudaStream_t st)
+{
+    if (storage == FDTD_STORAGE_F16) return launch_h<StoreF16>(f, nx, ny, nz, pitch, neg_dt, sc, st);
+    if (storage == FDTD_STORAGE_BF16) return launch_h<StoreBF16>(f, nx, ny, nz, pitch, neg_dt, sc, st);
+    return launch_h<StoreF32>(f, nx, ny, nz, pitch, neg_dt, sc, st);
+}
+
+cudaError_t launch_naive_e(void *const f[6], int storage, const float *ce, int nx, int ny, int nz, int pitch,
+                           long long step, const SrcSet &src, const Scales &sc, cudaStream_t st)
+{
+    if (storage == FDTD_STORAGE_F16) return launch_e<StoreF16>(f, ce, nx, ny, nz, pitch, step, src, sc, st);
+    if (storage == FDTD_STORAGE_BF16) return launch_e<StoreBF16>(f, ce, nx, ny, nz, pitch, step, src, sc, st);
+    return launch_e<StoreF32>(f, ce, nx, ny, nz, pitch, step, src, sc, st);
 }

@@ -51,12 +51,12 @@ fdtd_status setup_device(int dev, DeviceState *&out)
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-        e = systolic_configure(NOALLOC_VARIANT);
+        e = systolic_configure(NOALLOC_VARIANT, FDTD_STORAGE_F32);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-        const int per_sm = systolic_max_ctas_per_sm(NOALLOC_VARIANT);
+        const int per_sm = systolic_max_ctas_per_sm(NOALLOC_VARIANT, FDTD_STORAGE_F32);
         if (per_sm < 1) return FDTD_ERR_UNSUPPORTED;
         d.scratch = (unsigned char *)p;
         d.max_ctas = sms * per_sm;
@@ -126,7 +126,8 @@ extern "C" fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *
     p.nz = g.nz;
     p.pitch = g.nx;  // the caller's dense arrays
     p.fbase = d_fields;
-    p.fstride = 0;   // the coefficient is a separate buffer
+    p.fstride = (long long)n;
+    for (int c = 0; c < 6; ++c) p.sc.s[c] = p.sc.is[c] = 1.f;  // FP32 storage
     p.gx = gx;
     p.gy = gy;
     p.gz = gz;
@@ -153,7 +154,7 @@ extern "C" fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *
         p.step0 = step;
         p.ntiles = (int)count_le[(size_t)Tl];
         const int grid_ctas = (int)std::max<long long>(1, std::min<long long>(p.ntiles, ds->max_ctas));
-        if ((e = launch_systolic(p, grid_ctas, s, NOALLOC_VARIANT)) != cudaSuccess) return cuda_fail(e, "launch");
+        if ((e = launch_systolic(p, grid_ctas, s, NOALLOC_VARIANT, FDTD_STORAGE_F32)) != cudaSuccess) return cuda_fail(e, "launch");
         epoch += (unsigned)Tl + 1u;
         step += Tl;
         n_steps -= Tl;

@@ -29,7 +29,14 @@
 //
 // Tile: 31 x 15 x NZ updated cells.  Every arithmetic step is yee_cell.cuh,
 // so the result equals the naive schedule bit for bit.
+//
+// Storage: fields live in global memory as FP32, FP16 or BF16 (S, see
+// storage.cuh); registers hold FP32 values already rounded to the storage
+// format, so each new H value is rounded where it is computed and each new
+// E value once its point source (if any) has been added, exactly where the
+// naive schedule rounds on store.  dt/eps stays FP32.
 #include "internal.h"
+#include "storage.cuh"
 #include "sys_common.cuh"
 #include "yee_cell.cuh"
 
@@ -37,8 +44,10 @@ namespace {
 
 using namespace sysc;
 
-template <int NZ_>
+template <int NZ_, class S_>
 struct RegTile {
+    using S = S_;
+    using T = typename S_::T;
     static constexpr int NZ = NZ_;        // updated z rows (registers 0..NZ-1)
     static constexpr int NR = NZ_ + 1;    // plus the shell row -1
     static constexpr int RY = 16, NT = 32 * RY;
@@ -49,21 +58,29 @@ struct RegTile {
     static constexpr int XE_F = RY * NZ * 32;    // one exchanged component
     static constexpr int XO_F = RY * 6 * NZ;
     // lower-shell staging, filled per step by bulk tensor copies (TMA) of
-    // boxes whose x start is rounded down to 16 bytes: SW = 36 floats cover
-    // the 32-wide x window; every box starts on a 128-byte boundary
-    static constexpr int SW = 36;
-    static constexpr int ZB = RY * SW;                       // z shell box {36,16,1}: [y][x]
-    static constexpr int YB = (NR * SW * 4 + 127) / 128 * 32; // y shell box {36,1,NR}: [z][x], padded
-    static constexpr int XB = NR * 16 * 4;                   // x shell box {4,16,NR}: [z][y][x]
-    static_assert((ZB * 4) % 128 == 0 && (XB * 4) % 128 == 0, "boxes stay 128-byte aligned");
-    static constexpr int ZST_F = 7 * ZB, YST_F = 7 * YB, XST_F = 7 * XB;
-    static constexpr unsigned TMA_BYTES = 4u * 7u * (RY * SW + NR * SW + NR * 16 * 4);
+    // boxes whose x start is rounded down to 16 bytes (XA elements): SW =
+    // 32 + XA elements cover the 32-wide x window.  Fields use the storage
+    // element, the coefficient FP32 (C-suffixed sizes); every box starts on
+    // a 128-byte boundary.
+    static constexpr int EB = (int)sizeof(T);
+    static constexpr int XA = 16 / EB, SW = 32 + XA;
+    static constexpr int ZB = RY * SW;                                  // z shell box {SW,16,1}: [y][x]
+    static constexpr int YB = (NR * SW * EB + 127) / 128 * 128 / EB;   // y shell box {SW,1,NR}: [z][x], padded
+    static constexpr int XB = NR * 16 * XA;                            // x shell box {XA,16,NR}: [z][y][x]
+    static constexpr int XAC = 4, SWC = 36;
+    static constexpr int ZBC = RY * SWC, YBC = (NR * SWC * 4 + 127) / 128 * 32, XBC = NR * 16 * XAC;
+    static_assert((ZB * EB) % 128 == 0 && (XB * EB) % 128 == 0 && (YB * EB) % 128 == 0, "boxes stay 128-byte aligned");
+    static_assert((ZBC * 4) % 128 == 0 && (XBC * 4) % 128 == 0, "boxes stay 128-byte aligned");
+    static constexpr int FST_B = 6 * (ZB + YB + XB) * EB;  // field staging bytes
+    static constexpr int CST_F = ZBC + YBC + XBC;          // coefficient staging floats
+    static constexpr unsigned TMA_BYTES =
+        6u * EB * (RY * SW + NR * SW + NR * 16 * XA) + 4u * (RY * SWC + NR * SWC + NR * 16 * XAC);
     static constexpr int CR = 16;                 // coefficient ring rows (>= NR, power of 2)
     static constexpr int CE_F = RY * CR * 32;
     static_assert(CR >= NR, "coefficient ring holds the whole column");
     static constexpr size_t smem_bytes()
     {
-        return sizeof(float) * (4 * (size_t)XE_F + XO_F + CE_F + ZST_F + YST_F + XST_F);
+        return FST_B + sizeof(float) * (4 * (size_t)XE_F + XO_F + CE_F + CST_F);
     }
 };
 
@@ -109,14 +126,19 @@ __device__ bool wait_stage(const SysLaunch &P, unsigned long long *bar, unsigned
 template <class R>
 __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_constant__ SysLaunch P)
 {
+    using S = typename R::S;
+    using T = typename R::T;
     constexpr int NZ = R::NZ, NR = R::NR, TX = R::TX, TY = R::TY, TZ = R::TZ;
+    constexpr int SW = R::SW, XA = R::XA, SWC = R::SWC;
     extern __shared__ __align__(1024) float4 smem4[];
-    float *const sm = reinterpret_cast<float *>(smem4);
     // staging boxes first: the dynamic shared memory base is 1024-byte aligned
-    float *const ZST = sm;                 // lower z shell
-    float *const YST = ZST + R::ZST_F;     // lower y shell
-    float *const XST = YST + R::YST_F;     // lower x shell
-    float *const XEx = XST + R::XST_F;     // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
+    T *const ZST = reinterpret_cast<T *>(smem4);  // lower z shell, 6 fields
+    T *const YST = ZST + 6 * R::ZB;               // lower y shell
+    T *const XST = YST + 6 * R::YB;               // lower x shell
+    float *const ZSC = reinterpret_cast<float *>(reinterpret_cast<char *>(smem4) + R::FST_B);  // dt/eps shells
+    float *const YSC = ZSC + R::ZBC;
+    float *const XSC = YSC + R::YBC;
+    float *const XEx = XSC + R::XBC;       // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
     float *const XEz = XEx + R::XE_F;
     float *const XHx = XEz + R::XE_F;      // [warp][row i-1][lane]: new H rows r = 0..NZ-1
     float *const XHz = XHx + R::XE_F;
@@ -131,23 +153,35 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const float ndt = P.neg_dt;
     const long long sxy = (long long)P.pitch * P.ny;
-    // field pointers are read from the kernel parameters where used (they stay
-    // in the constant bank instead of taking 14 registers)
-#define F0 P.f[0]
-#define F1 P.f[1]
-#define F2 P.f[2]
-#define F3 P.f[3]
-#define F4 P.f[4]
-#define F5 P.f[5]
+    // field pointers and scales are read from the kernel parameters where
+    // used (they stay in the constant bank instead of taking registers)
+#define F0 reinterpret_cast<T *>(P.f[0])
+#define F1 reinterpret_cast<T *>(P.f[1])
+#define F2 reinterpret_cast<T *>(P.f[2])
+#define F3 reinterpret_cast<T *>(P.f[3])
+#define F4 reinterpret_cast<T *>(P.f[4])
+#define F5 reinterpret_cast<T *>(P.f[5])
 #define CE P.ce
+#define SC(c) P.sc.s[c]
+#define IS(c) P.sc.is[c]
+#define RND(v, c) S::rnd(v, SC(c), IS(c))
+#define STORE6(g, i)                                                                          \
+    do {                                                                                      \
+        F0[g] = S::enc(ex[i], IS(0)); F1[g] = S::enc(ey[i], IS(1)); F2[g] = S::enc(ez[i], IS(2)); \
+        F3[g] = S::enc(hx[i], IS(3)); F4[g] = S::enc(hy[i], IS(4)); F5[g] = S::enc(hz[i], IS(5)); \
+    } while (0)
 
     // Cooperative x-shell load and top x-face store: thread bits pick the
     // entry (row = tid & 15, field = (tid >> 4) & 7, warp offset = tid >> 7,
     // plus 4 per pass), so no division is needed.  Field c of the workspace
-    // is fbase + c*fstride (c = 6: dt/eps).
+    // is fbase + c*fstride elements.
     const int q_row = tid & 15, q_f = (tid >> 4) & 7, q_w = tid >> 7;
-    float *const FB = P.fbase;
+    T *const FB = reinterpret_cast<T *>(P.fbase);
     const long long FS = P.fstride;
+    // the inverse scale of this thread's x-face field, picked without a
+    // dynamically indexed parameter array
+    const float q_is = q_f == 0 ? IS(0) : q_f == 1 ? IS(1) : q_f == 2 ? IS(2) : q_f == 3 ? IS(3)
+                     : q_f == 4 ? IS(4) : IS(5);
 
     constexpr int CR = R::CR;
     if (tid == 0) {
@@ -203,8 +237,9 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 float c = 0.f;
                 if (cin && (unsigned)pz < (unsigned)P.nz) {
                     const long long g = col + sxy * pz;
-                    ex[i] = ld_cg(F0 + g); ey[i] = ld_cg(F1 + g); ez[i] = ld_cg(F2 + g);
-                    hx[i] = ld_cg(F3 + g); hy[i] = ld_cg(F4 + g); hz[i] = ld_cg(F5 + g);
+                    ex[i] = S::dec(S::ld_cg(F0 + g), SC(0)); ey[i] = S::dec(S::ld_cg(F1 + g), SC(1));
+                    ez[i] = S::dec(S::ld_cg(F2 + g), SC(2)); hx[i] = S::dec(S::ld_cg(F3 + g), SC(3));
+                    hy[i] = S::dec(S::ld_cg(F4 + g), SC(4)); hz[i] = S::dec(S::ld_cg(F5 + g), SC(5));
                     c = __ldg(CE + g);
                 } else {
                     ex[i] = ey[i] = ez[i] = hx[i] = hy[i] = hz[i] = 0.f;
@@ -253,8 +288,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                         const int qz = pbz + i - 1;
                         if ((unsigned)qz < (unsigned)P.nz) {
                             const long long g = c2 + sxy * qz;
-                            F0[g] = ex[i]; F1[g] = ey[i]; F2[g] = ez[i];
-                            F3[g] = hx[i]; F4[g] = hy[i]; F5[g] = hz[i];
+                            STORE6(g, i);
                         }
                     }
                 }
@@ -268,24 +302,27 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                         const int wv = (pby + wi) & (R::RY - 1);
                         const int qx = pbx + TX - 1, qy = pby + wi, qz = pbz + q_row;
                         if (in_dom(P, qx, qy, qz))
-                            FB[q_f * FS + gidx(P, qx, qy, qz)] = XO[(wv * 6 + q_f) * NZ + q_row];
+                            FB[q_f * FS + gidx(P, qx, qy, qz)] = S::enc(XO[(wv * 6 + q_f) * NZ + q_row], q_is);
                     }
                 }
             }
             // lower shells (level t) into shared staging: 21 bulk tensor copies
             // issued by one thread (x start rounded down to 16 bytes; zero fill
             // off the domain)
-            const int x0 = (bx - 1) & ~3;
+            const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1);
             if (tid == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_bar)),
                              "r"(R::TMA_BYTES) : "memory");
 #pragma unroll
-                for (int f = 0; f < 7; ++f) {
+                for (int f = 0; f < 6; ++f) {
                     tma_box(ZST + f * R::ZB, &P.tm[0][f], x0, by - 1, bz - 1, &s_bar);
                     tma_box(YST + f * R::YB, &P.tm[1][f], x0, by - 1, bz - 1, &s_bar);
                     tma_box(XST + f * R::XB, &P.tm[2][f], x0, by, bz - 1, &s_bar);
                 }
+                tma_box(ZSC, &P.tm[0][6], x0c, by - 1, bz - 1, &s_bar);
+                tma_box(YSC, &P.tm[1][6], x0c, by - 1, bz - 1, &s_bar);
+                tma_box(XSC, &P.tm[2][6], x0c, by, bz - 1, &s_bar);
             }
 
             // C. H half-step, top-down in place: H[i] <- H[i-1] - dt curl_f(E[i-1], E[i], ...)
@@ -302,9 +339,9 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     const float nhy = h_y(hy[i - 1], ex[i], ex[i - 1], ez_xp, ez[i - 1], ndt);
                     const float nhz = h_z(hz[i - 1], ey_xp, ey[i - 1], ex_yp, ex[i - 1], ndt);
                     const bool upd = colin && i >= i_lo && i < i_hi;
-                    hx[i] = upd ? nhx : hx[i - 1];
-                    hy[i] = upd ? nhy : hy[i - 1];
-                    hz[i] = upd ? nhz : hz[i - 1];
+                    hx[i] = upd ? RND(nhx, 3) : hx[i - 1];
+                    hy[i] = upd ? RND(nhy, 4) : hy[i - 1];
+                    hz[i] = upd ? RND(nhz, 5) : hz[i - 1];
                 }
             }
             if (!wait_stage(P, &s_bar, stage_phase & 1u, ticket)) s_abort = 1;
@@ -314,30 +351,35 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 
             // D. refills from the staged shells, then publish new H rows for the
             //    warp above's E half-step
-            const int xe = (bx - 1) - x0;  // x offset of the shell column in its chunk
+            const int xe = (bx - 1) - x0, xec = (bx - 1) - x0c;  // x offset of the shell column in its chunk
             if (w == ey_w) {  // the y shell warp takes its whole column set (level t)
-                const int xl = (bx - 1) + ((lane - bx + 1) & 31) - x0;
+                const int xw = (bx - 1) + ((lane - bx + 1) & 31);
+                const int xl = xw - x0, xlc = xw - x0c;
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
-                    ex[i] = YST[0 * R::YB + i * R::SW + xl]; ey[i] = YST[1 * R::YB + i * R::SW + xl];
-                    ez[i] = YST[2 * R::YB + i * R::SW + xl]; hx[i] = YST[3 * R::YB + i * R::SW + xl];
-                    hy[i] = YST[4 * R::YB + i * R::SW + xl]; hz[i] = YST[5 * R::YB + i * R::SW + xl];
-                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YST[6 * R::YB + i * R::SW + xl];
+                    ex[i] = S::dec(YST[0 * R::YB + i * SW + xl], SC(0));
+                    ey[i] = S::dec(YST[1 * R::YB + i * SW + xl], SC(1));
+                    ez[i] = S::dec(YST[2 * R::YB + i * SW + xl], SC(2));
+                    hx[i] = S::dec(YST[3 * R::YB + i * SW + xl], SC(3));
+                    hy[i] = S::dec(YST[4 * R::YB + i * SW + xl], SC(4));
+                    hz[i] = S::dec(YST[5 * R::YB + i * SW + xl], SC(5));
+                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YSC[i * SWC + xlc];
                 }
             } else if (xbox) {  // row -1 takes the lower z shell's H and coefficient
-                const int o = (dy + 1) * R::SW + (px - x0);
-                hx[0] = ZST[3 * R::ZB + o];
-                hy[0] = ZST[4 * R::ZB + o];
-                hz[0] = ZST[5 * R::ZB + o];
-                CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZST[6 * R::ZB + o];
+                const int o = (dy + 1) * SW + (px - x0), oc = (dy + 1) * SWC + (px - x0c);
+                hx[0] = S::dec(ZST[3 * R::ZB + o], SC(3));
+                hy[0] = S::dec(ZST[4 * R::ZB + o], SC(4));
+                hz[0] = S::dec(ZST[5 * R::ZB + o], SC(5));
+                CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZSC[oc];
             } else {  // the lane leaving the tile in x takes the x shell's H and coefficient
-                const float *xs = XST + dy * 4 + xe;
+                const T *xs = XST + dy * XA + xe;
+                const float *xsc = XSC + dy * R::XAC + xec;
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
-                    hx[i] = xs[3 * R::XB + i * 64];
-                    hy[i] = xs[4 * R::XB + i * 64];
-                    hz[i] = xs[5 * R::XB + i * 64];
-                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xs[6 * R::XB + i * 64];
+                    hx[i] = S::dec(xs[3 * R::XB + i * 16 * XA], SC(3));
+                    hy[i] = S::dec(xs[4 * R::XB + i * 16 * XA], SC(4));
+                    hz[i] = S::dec(xs[5 * R::XB + i * 16 * XA], SC(5));
+                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xsc[i * 16 * R::XAC];
                 }
             }
 #pragma unroll
@@ -347,6 +389,18 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             }
             __syncthreads();  // B2
             if (t > iv.s && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)t);  // level t-1 done
+
+            // does this thread own a point source this step?  (16-bit storage:
+            // its E rows are rounded after the source is added, not before)
+            const long long step = P.step0 + t;
+            bool srcthr = false;
+            if (S::narrow) {
+                for (int q = 0; q < P.src.n; ++q) {
+                    const SrcDesc &s = P.src.s[q];
+                    srcthr |= step < s.n_amp && s.i >= bx && s.i < bx + TX && s.j >= by && s.j < by + TY &&
+                              s.k >= bz && s.k < bz + TZ && lane == (s.i & 31) && w == (s.j & (R::RY - 1));
+                }
+            }
 
             if (w != ey_w) {
                 // F. E half-step, top-down in place: E[i] <- E[i-1] + ce curl_b(H[i], H[i-1], ...)
@@ -365,44 +419,49 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     const float nez = e_z(ez[i - 1], hy[i], hy_xm, hx[i], hx_ym, c);
                     const bool in = colin && i >= i_lo && i < i_hi;
                     const bool kz = bz + i - 1 > 0;
-                    ex[i] = (in && ux && kz) ? nex : ex[i - 1];
-                    ey[i] = (in && uy && kz) ? ney : ey[i - 1];
-                    ez[i] = (in && uz) ? nez : ez[i - 1];
+                    ex[i] = (in && ux && kz) ? (srcthr ? nex : RND(nex, 0)) : ex[i - 1];
+                    ey[i] = (in && uy && kz) ? (srcthr ? ney : RND(ney, 1)) : ey[i - 1];
+                    ez[i] = (in && uz) ? (srcthr ? nez : RND(nez, 2)) : ez[i - 1];
                 }
                 if (xbox) {  // row -1 takes the lower z shell's E (level t)
-                    const int o = (dy + 1) * R::SW + (px - x0);
-                    ex[0] = ZST[0 * R::ZB + o];
-                    ey[0] = ZST[1 * R::ZB + o];
-                    ez[0] = ZST[2 * R::ZB + o];
+                    const int o = (dy + 1) * SW + (px - x0);
+                    ex[0] = S::dec(ZST[0 * R::ZB + o], SC(0));
+                    ey[0] = S::dec(ZST[1 * R::ZB + o], SC(1));
+                    ez[0] = S::dec(ZST[2 * R::ZB + o], SC(2));
                 } else {  // the x lane takes the rest of its shell column
-                    const float *xs = XST + dy * 4 + xe;
+                    const T *xs = XST + dy * XA + xe;
 #pragma unroll
                     for (int i = 0; i < NR; ++i) {
-                        ex[i] = xs[0 * R::XB + i * 64];
-                        ey[i] = xs[1 * R::XB + i * 64];
-                        ez[i] = xs[2 * R::XB + i * 64];
+                        ex[i] = S::dec(xs[0 * R::XB + i * 16 * XA], SC(0));
+                        ey[i] = S::dec(xs[1 * R::XB + i * 16 * XA], SC(1));
+                        ez[i] = S::dec(xs[2 * R::XB + i * 16 * XA], SC(2));
                     }
                 }
             }
 
             // point sources inside the box: the owning thread adds them
-            {
-                const long long step = P.step0 + t;
-                for (int q = 0; q < P.src.n; ++q) {
-                    const SrcDesc &s = P.src.s[q];
-                    if (step < s.n_amp && s.i >= bx && s.i < bx + TX && s.j >= by && s.j < by + TY &&
-                        s.k >= bz && s.k < bz + TZ && lane == (s.i & 31) && w == (s.j & (R::RY - 1))) {
-                        const float a = s.amp[step];
-                        const int ri = s.k - bz + 1;
+            for (int q = 0; q < P.src.n; ++q) {
+                const SrcDesc &s = P.src.s[q];
+                if (step < s.n_amp && s.i >= bx && s.i < bx + TX && s.j >= by && s.j < by + TY &&
+                    s.k >= bz && s.k < bz + TZ && lane == (s.i & 31) && w == (s.j & (R::RY - 1))) {
+                    const float a = s.amp[step];
+                    const int ri = s.k - bz + 1;
 #pragma unroll
-                        for (int i = 1; i < NR; ++i) {
-                            if (i == ri) {
-                                if (s.comp == 0) ex[i] = add_source(ex[i], a);
-                                else if (s.comp == 1) ey[i] = add_source(ey[i], a);
-                                else ez[i] = add_source(ez[i], a);
-                            }
+                    for (int i = 1; i < NR; ++i) {
+                        if (i == ri) {
+                            if (s.comp == 0) ex[i] = add_source(ex[i], a);
+                            else if (s.comp == 1) ey[i] = add_source(ey[i], a);
+                            else ez[i] = add_source(ez[i], a);
                         }
                     }
+                }
+            }
+            if (S::narrow && srcthr) {  // one rounding per value, as the naive schedule stores it
+#pragma unroll
+                for (int i = 1; i < NR; ++i) {
+                    ex[i] = RND(ex[i], 0);
+                    ey[i] = RND(ey[i], 1);
+                    ez[i] = RND(ez[i], 2);
                 }
             }
 
@@ -413,8 +472,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     for (int i = 1; i < NR; ++i) {
                         if (i >= i_lo && i < i_hi) {
                             const long long g = col + sxy * (bz + i - 1);
-                            F0[g] = ex[i]; F1[g] = ey[i]; F2[g] = ez[i];
-                            F3[g] = hx[i]; F4[g] = hy[i]; F5[g] = hz[i];
+                            STORE6(g, i);
                         }
                     }
                 }
@@ -423,8 +481,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     // (the top y face is stored next step by the warp holding it)
                     if (NR - 1 >= i_lo && NR - 1 < i_hi) {  // top z face
                         const long long g = col + sxy * (bz + NR - 2);
-                        F0[g] = ex[NR - 1]; F1[g] = ey[NR - 1]; F2[g] = ez[NR - 1];
-                        F3[g] = hx[NR - 1]; F4[g] = hy[NR - 1]; F5[g] = hz[NR - 1];
+                        STORE6(g, NR - 1);
                     }
                 }
                 if (ybox && dx == TX - 1) {  // top x face: staged, stored at B1 of the next step
@@ -461,8 +518,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     const int qz = pbz + i - 1;
                     if ((unsigned)qz < (unsigned)P.nz) {
                         const long long g = c2 + sxy * qz;
-                        F0[g] = ex[i]; F1[g] = ey[i]; F2[g] = ez[i];
-                        F3[g] = hx[i]; F4[g] = hy[i]; F5[g] = hz[i];
+                        STORE6(g, i);
                     }
                 }
             }
@@ -476,7 +532,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     const int wv = (pby + wi) & (R::RY - 1);
                     const int qx = pbx + TX - 1, qy = pby + wi, qz = pbz + q_row;
                     if (in_dom(P, qx, qy, qz))
-                        FB[q_f * FS + gidx(P, qx, qy, qz)] = XO[(wv * 6 + q_f) * NZ + q_row];
+                        FB[q_f * FS + gidx(P, qx, qy, qz)] = S::enc(XO[(wv * 6 + q_f) * NZ + q_row], q_is);
                 }
             }
         }
@@ -492,43 +548,72 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #undef F4
 #undef F5
 #undef CE
+#undef SC
+#undef IS
+#undef RND
+#undef STORE6
 
-using RegA = RegTile<12>;  // 31 x 15 x 12
-using RegB = RegTile<8>;   // 31 x 15 x 8
+// 31 x 15 x 12 and 31 x 15 x 8 tiles, each for the three storage formats
+template <int NZ>
+struct RegShape {
+    static cudaError_t configure(int storage)
+    {
+        if (storage == FDTD_STORAGE_F16) return set<RegTile<NZ, StoreF16>>();
+        if (storage == FDTD_STORAGE_BF16) return set<RegTile<NZ, StoreBF16>>();
+        return set<RegTile<NZ, StoreF32>>();
+    }
+    static int per_sm(int storage)
+    {
+        if (storage == FDTD_STORAGE_F16) return occ<RegTile<NZ, StoreF16>>();
+        if (storage == FDTD_STORAGE_BF16) return occ<RegTile<NZ, StoreBF16>>();
+        return occ<RegTile<NZ, StoreF32>>();
+    }
+    static cudaError_t launch(const SysLaunch &p, int grid, cudaStream_t st, int storage)
+    {
+        if (storage == FDTD_STORAGE_F16) return go<RegTile<NZ, StoreF16>>(p, grid, st);
+        if (storage == FDTD_STORAGE_BF16) return go<RegTile<NZ, StoreBF16>>(p, grid, st);
+        return go<RegTile<NZ, StoreF32>>(p, grid, st);
+    }
+    template <class R>
+    static cudaError_t set()
+    {
+        return cudaFuncSetAttribute(systolic_reg_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)R::smem_bytes());
+    }
+    template <class R>
+    static int occ()
+    {
+        int n = 0;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_reg_kernel<R>, R::NT, R::smem_bytes()) ==
+                       cudaSuccess
+                   ? n
+                   : 0;
+    }
+    template <class R>
+    static cudaError_t go(const SysLaunch &p, int grid, cudaStream_t st)
+    {
+        systolic_reg_kernel<R><<<grid, R::NT, R::smem_bytes(), st>>>(p);
+        return cudaGetLastError();
+    }
+};
+
+using RegA = RegShape<12>;  // 31 x 15 x 12
+using RegB = RegShape<8>;   // 31 x 15 x 8
 
 } // namespace
 
-int systolic_reg_rows(int k) { return k == 0 ? RegA::NR : RegB::NR; }
+int systolic_reg_rows(int k) { return (k == 0 ? 12 : 8) + 1; }
 
-SysShape systolic_reg_shape(int k)
+SysShape systolic_reg_shape(int k) { return SysShape{31, 15, k == 0 ? 12 : 8}; }
+
+cudaError_t systolic_reg_configure(int k, int storage)
 {
-    return k == 0 ? SysShape{RegA::TX, RegA::TY, RegA::TZ} : SysShape{RegB::TX, RegB::TY, RegB::TZ};
+    return k == 0 ? RegA::configure(storage) : RegB::configure(storage);
 }
 
-cudaError_t systolic_reg_configure(int k)
-{
-    if (k == 0)
-        return cudaFuncSetAttribute(systolic_reg_kernel<RegA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)RegA::smem_bytes());
-    return cudaFuncSetAttribute(systolic_reg_kernel<RegB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)RegB::smem_bytes());
-}
+int systolic_reg_max_ctas_per_sm(int k, int storage) { return k == 0 ? RegA::per_sm(storage) : RegB::per_sm(storage); }
 
-int systolic_reg_max_ctas_per_sm(int k)
+cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int storage)
 {
-    int n = 0;
-    cudaError_t e = k == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_reg_kernel<RegA>, RegA::NT,
-                                                                          RegA::smem_bytes())
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, systolic_reg_kernel<RegB>, RegB::NT,
-                                                                          RegB::smem_bytes());
-    return e == cudaSuccess ? n : 0;
-}
-
-cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k)
-{
-    if (k == 0)
-        systolic_reg_kernel<RegA><<<grid, RegA::NT, RegA::smem_bytes(), st>>>(p);
-    else
-        systolic_reg_kernel<RegB><<<grid, RegB::NT, RegB::smem_bytes(), st>>>(p);
-    return cudaGetLastError();
+    return k == 0 ? RegA::launch(p, grid, st, storage) : RegB::launch(p, grid, st, storage);
 }

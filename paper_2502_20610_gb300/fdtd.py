@@ -113,7 +113,7 @@ TILES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15), "31x15x12": (31, 15, 
 
 
 def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
-                steps_per_launch=0, max_source_steps=0, boundary="pec", tile=None):
+                steps_per_launch=0, max_source_steps=0, boundary="pec", tile=None, field_scale=None):
     nz, ny, nx = (int(s) for s in shape_zyx)
     g = Grid(nx, ny, nz)
     c = Coeffs()
@@ -121,7 +121,7 @@ def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
     c.scheme = SCHEMES[scheme]
     c.storage = STORAGE[storage]
     for a in range(6):
-        c.field_scale[a] = 1.0
+        c.field_scale[a] = 1.0 if field_scale is None else float(field_scale[a])
     c.wait_timeout_s = float(timeout_s)
     c.steps_per_launch = int(steps_per_launch)
     c.max_source_steps = int(max_source_steps)
@@ -158,21 +158,24 @@ class Sim:
     """One simulation: (nz, ny, nx) grid, per-cell eps, PEC box.
 
     scheme: "naive" (one kernel per half-step) or "systolic" (persistent
-    skewed-tile kernel).  Fields are exchanged as float32 (6, nz, ny, nx)
-    arrays in component order Ex, Ey, Ez, Hx, Hy, Hz.
+    skewed-tile kernel).  storage: "f32", "f16" or "bf16" field storage
+    (arithmetic is FP32 in every case); field_scale: six powers of two, the
+    16-bit formats store v / s_c.  Fields are exchanged as float32
+    (6, nz, ny, nx) arrays in component order Ex, Ey, Ez, Hx, Hy, Hz.
     """
 
     def __init__(self, shape_zyx, eps, dt, scheme="systolic", device=None, timeout_s=2.0,
-                 steps_per_launch=0, max_source_steps=0, tile=None):
+                 steps_per_launch=0, max_source_steps=0, tile=None, storage="f32", field_scale=None):
         import torch
         self._lib = load_library()
         self.shape = tuple(int(s) for s in shape_zyx)
         self.dt = float(dt)
         self.scheme = scheme
+        self.storage = storage
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         g, c, b = make_params(self.shape, dt, scheme=scheme, timeout_s=timeout_s,
                               steps_per_launch=steps_per_launch, max_source_steps=max_source_steps,
-                              tile=tile)
+                              tile=tile, storage=storage, field_scale=field_scale)
         self._params = (g, c, b)
         n = ctypes.c_size_t(0)
         _check(self._lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c), ctypes.byref(b),
@@ -258,3 +261,24 @@ class Sim:
     def debug_set(self, kind, ticket=0, param=0, param2=0):
         _check(self._lib.fdtd_debug_set(self._h, int(kind), int(ticket), int(param), int(param2)),
                "fdtd_debug_set")
+
+
+def field_scales(fields, storage, headroom=4):
+    """Power-of-two scales s_c for FP16 storage, chosen from the initial
+    fields: the largest |v_c| / s_c lands in [2^(14 - headroom), 2^(15 -
+    headroom)), leaving 2^headroom of room for growth below the binary16
+    maximum (65504) while keeping small values out of the subnormal range
+    (below 2^-14).  All-zero components get 1.  FP32 and BF16 (whose
+    exponent range is FP32's): all 1."""
+    if storage != "f16":
+        return [1.0] * 6
+    top = 15
+    out = []
+    for c in range(6):
+        m = float(np.max(np.abs(np.asarray(fields[c], dtype=np.float64)))) if np.size(fields[c]) else 0.0
+        if not np.isfinite(m) or m == 0.0:
+            out.append(1.0)
+            continue
+        e = int(np.floor(np.log2(m)))  # 2^e <= m < 2^(e+1)
+        out.append(float(2.0 ** min(100, max(-100, e + 1 - (top - headroom)))))
+    return out

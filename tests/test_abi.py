@@ -57,6 +57,38 @@ def test_workspace_size_and_argument_checks(lib):
         fdtd.FDTD_ERR_INVALID_ARG
 
 
+def _ws(lib, g, c, b):
+    n = ctypes.c_size_t(0)
+    st = lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c), ctypes.byref(b), ctypes.byref(n))
+    return st, n.value
+
+
+def test_storage_option_checks(lib):
+    shape = (32, 48, 64)
+    st32, n32 = _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive"))
+    for storage in ("f16", "bf16"):
+        st, n16 = _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive", storage=storage))
+        assert st == 0 and st32 == 0
+        # 6 fields at 2 bytes + FP32 dt/eps + one FP32 transfer component
+        assert n16 < n32 and n16 >= (6 * 2 + 4 + 4) * 32 * 48 * 64
+        st, _ = _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, storage=storage, tile="31x15x12"))
+        assert st == 0
+        # the shared-memory systolic kernels hold FP32 only
+        st, _ = _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, storage=storage, tile="31x15x15"))
+        assert st == fdtd.FDTD_ERR_UNSUPPORTED
+        for bad in (3.0, -2.0, float("inf"), float("nan"), 2.0 ** 120):
+            sc = [1.0] * 6
+            sc[4] = bad
+            st, _ = _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, storage=storage, field_scale=sc))
+            assert st == fdtd.FDTD_ERR_INVALID_ARG, bad
+        st, _ = _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, storage=storage,
+                                           field_scale=[0.0, 0.5, 2.0, 2.0 ** -20, 1.0, 8.0]))
+        assert st == 0
+    g, c, b = fdtd.make_params(shape, wl.DT_DEFAULT)
+    c.storage = 3
+    assert _ws(lib, g, c, b)[0] == fdtd.FDTD_ERR_INVALID_ARG
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.fdtd_step(None, 1) == fdtd.FDTD_ERR_INVALID_ARG
     assert lib.fdtd_current_step(None) == -1
