@@ -255,6 +255,107 @@ def time_storage_variant(shape, eps, J, src, storage, device, stream, n_calls=1)
     return out
 
 
+def naive_threads(shape):
+    """Threads the library's naive scheme launches on a (nz, ny, nx) grid: one
+    per cell in a single CTA up to 1024 cells, else 32 x 8 CTAs in x-y with
+    each thread marching 8 cells in z."""
+    nz, ny, nx = shape
+    cells = nx * ny * nz
+    if cells <= 1024:
+        return (cells + 31) // 32 * 32
+    return -(-nx // 32) * -(-ny // 8) * -(-nz // 8) * 256
+
+
+def sweep_shapes(min_cells=32, max_cells=1 << 28):
+    """Grids whose cell counts double from min_cells to max_cells, as
+    balanced as powers of two allow (x >= y >= z)."""
+    out = []
+    m = int(math.log2(min_cells))
+    while (1 << m) <= max_cells:
+        a = [m // 3 + (1 if r < m % 3 else 0) for r in range(3)]  # x, y, z exponents
+        out.append((1 << a[2], 1 << a[1], 1 << a[0]))
+        m += 1
+    return out
+
+
+def run_sweep(args):
+    """Size sweeps through the C ABI, one JSON line per measurement.
+    fig1: the naive schedule (FP32) on grids from ~1 KB to a few GB of field
+    state, per-thread and total throughput (Fig. 1), with the systolic
+    schedule beside it.  sizes: 128^3 .. 1024^3 of the Si/SiO2 workload with
+    FP32, FP16 and BF16 field storage, both schedules, 1000 steps each."""
+    import torch
+    from paper_2502_20610_gb300 import fdtd
+    from paper_2502_20610_gb300 import workloads as wl
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(device)
+    props = torch.cuda.get_device_properties(device)
+    info = {"sm_count": props.multi_processor_count,
+            "l2_bytes": getattr(props, "L2_cache_size", None),
+            "smem_per_block_optin": getattr(props, "shared_memory_per_block_optin", None)}
+    print(json.dumps({"sweep": args.sweep, "device": props.name, **info}), flush=True)
+
+    def measure(shape, scheme, storage, steps, eps, src=None, J=None):
+        cells = shape[0] * shape[1] * shape[2]
+        sim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme=scheme, device=device, storage=storage,
+                       steps_per_launch=min(steps, 1024), max_source_steps=max(steps, 1) if J is not None else 0)
+        if src is not None:
+            sim.add_source(*src, J[:steps])
+        warm = max(1, steps // 20)
+        sim.step(warm)
+        sim.sync()
+        sim.set_current_step(0)
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        l0 = sim.launch_count
+        start.record(stream)
+        sim.step(steps)
+        end.record(stream)
+        end.synchronize()
+        sim.sync()
+        t = start.elapsed_time(end) / 1e3
+        launches = sim.launch_count - l0
+        sim.close()
+        return cells * steps / t / 1e9, t, launches
+
+    if args.sweep == "fig1":
+        for shape in sweep_shapes(32, 1 << args.sweep_max_log2):
+            cells = shape[0] * shape[1] * shape[2]
+            steps = int(min(20000, max(200, 4e9 / cells / 10)))
+            eps = np.ones(shape)
+            row = {"grid_xyz": list(shape[::-1]), "cells": cells, "bytes_fields": 24 * cells, "steps": steps}
+            g, t, nl = measure(shape, "naive", "f32", steps, eps)
+            thr = naive_threads(shape)
+            resident = min(thr, info["sm_count"] * 2048)  # at most 2048 resident threads per SM
+            row.update({"naive_gcups": g, "naive_threads": thr, "naive_launches": nl,
+                        "naive_updates_per_us_per_thread": g * 1e3 / thr,
+                        "naive_resident_threads": resident,
+                        "naive_updates_per_us_per_resident_thread": g * 1e3 / resident})
+            if cells >= 1024:
+                row["systolic_gcups"] = measure(shape, "systolic", "f32", steps, eps)[0]
+            print(json.dumps(row), flush=True)
+        return 0
+    # sizes: the Si/SiO2 workload at 128^3 .. 1024^3, three storage formats
+    steps = args.steps_per_call if args.steps_per_call != STEPS_PER_CALL else 1000
+    for n in (128, 256, 512, 768, 1024):
+        shape = (n, n, n)
+        eps = wl.si_sio2_eps(shape, 1)
+        J = wl.sine_source(steps, wl.DT_DEFAULT, WAVELENGTH)
+        src = (2, n // 2, n // 2, n // 2)
+        for storage in ("f32", "f16", "bf16"):
+            eb = STORAGE_BYTES[storage]
+            for scheme in ("systolic", "naive"):
+                g, t, nl = measure(shape, scheme, storage, steps, eps, src, J)
+                b = systolic_bytes(DEFAULT_TILE, eb) if scheme == "systolic" else naive_bytes(eb)
+                print(json.dumps({"grid": n, "storage": storage, "scheme": scheme, "steps": steps, "gcups": g,
+                                  "seconds": t, "launches": nl, "algorithmic_bytes_per_cell_step": round(b, 3),
+                                  "stream_bound_gcups": load_peaks()[0] / (12.0 * eb),
+                                  "stream_frac": g / (load_peaks()[0] / (12.0 * eb))}), flush=True)
+            torch.cuda.empty_cache()
+    return 0
+
+
 def time_calls(sim, n_calls, stream):
     import torch
     start = torch.cuda.Event(enable_timing=True)
@@ -284,12 +385,17 @@ def main():
     ap.add_argument("--tile", default=None, help="systolic tile shape, e.g. 31x15x15 (default: library's)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"], help="field storage format")
     ap.add_argument("--no-16bit", action="store_true", help="skip the FP16/BF16 storage context lines")
+    ap.add_argument("--sweep", default=None, choices=["fig1", "sizes"],
+                    help="print size-sweep lines instead of the benchmark line")
+    ap.add_argument("--sweep-max-log2", type=int, default=28, help="fig1: largest grid, log2 of cells")
     args = ap.parse_args()
     GRID = (args.grid,) * 3
     STEPS_PER_CALL = args.steps_per_call
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.sweep:
+        return run_sweep(args)
 
     import torch
     from paper_2502_20610_gb300 import fdtd

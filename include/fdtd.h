@@ -25,6 +25,13 @@
  *   * Boundary: PEC box [0,N]^3.  Tangential E on the three low planes is
  *     never updated; E at index N reads as 0.
  *   * State after n steps is (E^n, H^{n-1/2}); fdtd_step advances whole steps.
+ *   * Field storage: FP32, or FP16 / BF16 with one power-of-two scale s_c per
+ *     component (the paper's engine keeps 16-bit fields, Sec. 4): component
+ *     c holds q = fl16(v / s_c), and every curl and accumulation runs in FP32
+ *     on decoded values; each new value is rounded once (to nearest even)
+ *     when stored, after its point source if it has one.  Both schedules
+ *     round at the same points and stay bit-identical.  dt/eps is FP32 in
+ *     every format.  The API always exchanges unscaled FP32 values.
  *   * Every call returns an fdtd_status and never aborts or exits.
  *   * Pointers: "host" = host memory; "device" = CUDA device memory of the
  *     current device; "any" = either (the CUDA runtime's unified addressing
@@ -65,8 +72,9 @@ typedef struct { int32_t nx, ny, nz; } fdtd_grid;
 typedef struct {
     double dt;                /* time step; > 0; Courant limit dt < 1/sqrt(3) */
     int32_t scheme;           /* FDTD_SCHEME_* */
-    int32_t storage;          /* FDTD_STORAGE_*; this build: F32 only */
-    float field_scale[6];     /* 16-bit storage scales (powers of two); unused for F32 */
+    int32_t storage;          /* FDTD_STORAGE_*; the systolic 31x15x15 and 31x7x15 tiles take F32 only */
+    float field_scale[6];     /* 16-bit storage: s_c, a power of two in [2^-100, 2^100], 0 = 1;
+                                 unused for F32.  Equal scales are fastest. */
     int32_t tile[3];          /* systolic subdomain (updated cells per axis); 0 = default */
     int32_t cluster[3];       /* systolic cluster shape; 0 = default (1,1,1) */
     double wait_timeout_s;    /* bound on any device-side wait; <= 0 = 2 s */
@@ -85,8 +93,10 @@ typedef struct {
 typedef struct fdtd_sim *fdtd_handle;
 
 /* Bytes of device workspace a simulation with these parameters needs.
- * Layout inside it is private.  Errors: INVALID_ARG (null pointer, grid
- * dimension < 1, dt <= 0), UNSUPPORTED (storage or boundary not built). */
+ * Layout inside it is private (16-bit storage adds one dense FP32 component
+ * for host transfers).  Errors: INVALID_ARG (null pointer, grid dimension
+ * < 1, dt <= 0, a field scale that is not a power of two), UNSUPPORTED
+ * (storage, tile or boundary not built). */
 fdtd_status fdtd_workspace_size(const fdtd_grid *grid, const fdtd_coeffs *coeffs,
                                 const fdtd_boundary *boundary, size_t *bytes);
 
@@ -114,12 +124,16 @@ fdtd_status fdtd_add_source(fdtd_handle h, int32_t component, int32_t i, int32_t
                             const double *J, int64_t n_steps);
 
 /* Overwrite all six fields with 6*nx*ny*nz floats (component-major, order
- * Ex..Hz) from `src` (any).  Asynchronous on the handle's stream; `src` must
- * stay valid until the stream reaches this point.  Clears an earlier device
- * error.  Leaves the step counter unchanged.  Errors: INVALID_ARG, CUDA. */
+ * Ex..Hz) from `src` (any).  16-bit storage rounds each value v to
+ * fl16(v / s_c) (to nearest even).  Asynchronous on the handle's stream;
+ * `src` must stay valid until the stream reaches this point.  Clears an
+ * earlier device error.  Leaves the step counter unchanged.
+ * Errors: INVALID_ARG, CUDA. */
 fdtd_status fdtd_write_fields(fdtd_handle h, const float *src);
 
-/* Advance n >= 0 whole steps with the handle's scheme.  Asynchronous:
+/* Advance n >= 0 whole steps with the handle's scheme (the naive scheme runs
+ * a grid of at most 1024 cells in one thread block per call, with block
+ * barriers between the half-steps).  Asynchronous:
  * returns once the kernels are enqueued; launch errors are returned here,
  * device-side wait timeouts at the next fdtd_sync / fdtd_read_fields.
  * Errors: INVALID_ARG (n < 0), STATE (an earlier device error not cleared
@@ -127,7 +141,8 @@ fdtd_status fdtd_write_fields(fdtd_handle h, const float *src);
 fdtd_status fdtd_step(fdtd_handle h, int64_t n);
 
 /* Copy the components selected by `component_mask` (bit c = component c) as
- * FP32, packed in component order, nx*ny*nz floats each, into `dst` (any).
+ * FP32 (16-bit storage: s_c * q, exact), packed in component order,
+ * nx*ny*nz floats each, into `dst` (any).
  * Synchronises the stream and checks the device error word first.
  * Errors: INVALID_ARG, TIMEOUT (a device wait ran out; no data copied), CUDA. */
 fdtd_status fdtd_read_fields(fdtd_handle h, uint32_t component_mask, float *dst);

@@ -263,6 +263,7 @@ struct fdtd_sim {
     float *ce;
     float *stage;  // dense FP32 component (16-bit storage), else null
     Scales sc;
+    int fmt;       // kernel format (storage.cuh): the storage, or its uniform-scale variant
     float *src_tab;
     unsigned *progress;
     int *tiles;
@@ -378,6 +379,15 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
         h->sc.s[k] = sk;
         h->sc.is[k] = 1.f / sk;  // exact: sk is a power of two
     }
+    // one scale for all six components: the kernels step the stored values
+    bool uniform = true;
+    for (int k = 1; k < 6; ++k) uniform = uniform && h->sc.s[k] == h->sc.s[0];
+    h->fmt = coeffs->storage;
+    h->sc.src = 1.f;
+    if (coeffs->storage != FDTD_STORAGE_F32 && uniform) {
+        h->fmt = coeffs->storage == FDTD_STORAGE_F16 ? FMT_F16U : FMT_BF16U;
+        h->sc.src = h->sc.is[0];
+    }
     h->src_tab = (float *)(h->ws + L.src);
     h->progress = (unsigned *)(h->ws + L.progress);
     h->tiles = (int *)(h->ws + L.tiles);
@@ -413,13 +423,13 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     if (e != cudaSuccess) return fail(cuda_status(e));
 
     if (coeffs->scheme == FDTD_SCHEME_SYSTOLIC) {
-        e = systolic_configure(L.variant, coeffs->storage);
+        e = systolic_configure(L.variant, h->fmt);
         if (e != cudaSuccess) return fail(cuda_status(e));
         int dev = 0, sms = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return fail(cuda_status(e));
-        const int per_sm = systolic_max_ctas_per_sm(L.variant, coeffs->storage);
+        const int per_sm = systolic_max_ctas_per_sm(L.variant, h->fmt);
         if (per_sm < 1) return fail(FDTD_ERR_UNSUPPORTED);
         h->max_ctas = sms * per_sm;
         if (L.variant >= 2) {
@@ -496,9 +506,21 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
     if (h->failed) return FDTD_ERR_STATE;
     if (h->c.scheme == FDTD_SCHEME_NAIVE) {
         const float ndt = -(float)h->c.dt;
+        const long long cells = (long long)h->g.nx * h->g.ny * h->g.nz;
+        if (cells <= naive_block_max_cells()) {  // one CTA holds the domain: no global sync
+            while (n > 0) {
+                const int T = (int)std::min<int64_t>(n, 1 << 20);
+                CK(launch_naive_block(h->f, h->fmt, h->ce, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->step, T,
+                                      h->src, h->sc, h->stream));
+                h->launches += 1;
+                h->step += T;
+                n -= T;
+            }
+            return FDTD_OK;
+        }
         for (int64_t s = 0; s < n; ++s) {
-            CK(launch_naive_h(h->f, h->c.storage, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->sc, h->stream));
-            CK(launch_naive_e(h->f, h->c.storage, h->ce, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->step, h->src,
+            CK(launch_naive_h(h->f, h->fmt, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->sc, h->stream));
+            CK(launch_naive_e(h->f, h->fmt, h->ce, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->step, h->src,
                               h->sc, h->stream));
             h->launches += 2;
             h->step += 1;
@@ -542,7 +564,7 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         p.src = h->src;
         if (h->L.variant >= 2) std::memcpy(p.tm, h->tm, sizeof(p.tm));
         const int grid = (int)std::max<long long>(1, std::min<long long>(p.ntiles, h->max_ctas));
-        CK(launch_systolic(p, grid, h->stream, h->L.variant, h->c.storage));
+        CK(launch_systolic(p, grid, h->stream, h->L.variant, h->fmt));
         h->launches += 1;
         h->epoch += (unsigned)T + 1u;
         h->step += T;

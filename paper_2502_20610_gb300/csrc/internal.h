@@ -30,12 +30,21 @@ struct SrcSet {
 };
 
 // Naive scheme: one H launch and one E launch per step.
-// Arrays are nx*ny*nz cells with rows of `pitch` elements (pitch >= nx) of
-// the storage format `storage` (FDTD_STORAGE_*); dt/eps is always FP32.
-cudaError_t launch_naive_h(void *const f[6], int storage, int nx, int ny, int nz, int pitch, float neg_dt,
+// Arrays are nx*ny*nz cells with rows of `pitch` elements (pitch >= nx) in
+// kernel format `fmt` (FDTD_STORAGE_* or FMT_*U of storage.cuh); dt/eps is
+// always FP32.
+cudaError_t launch_naive_h(void *const f[6], int fmt, int nx, int ny, int nz, int pitch, float neg_dt,
                            const Scales &sc, cudaStream_t st);
-cudaError_t launch_naive_e(void *const f[6], int storage, const float *ce, int nx, int ny, int nz, int pitch,
+cudaError_t launch_naive_e(void *const f[6], int fmt, const float *ce, int nx, int ny, int nz, int pitch,
                            long long step, const SrcSet &src, const Scales &sc, cudaStream_t st);
+
+// Naive scheme on a domain of at most naive_block_max_cells() cells: one
+// CTA, one thread per cell, `nsteps` steps in one launch (block barriers
+// between the half-steps).
+int naive_block_max_cells();
+cudaError_t launch_naive_block(void *const f[6], int fmt, const float *ce, int nx, int ny, int nz, int pitch,
+                               float neg_dt, long long step0, int nsteps, const SrcSet &src, const Scales &sc,
+                               cudaStream_t st);
 
 // FP32 <-> storage conversion of one component (convert.cu): `dense` holds
 // nx*ny*nz values, `pitched` rows of `pitch` elements.
@@ -53,8 +62,8 @@ struct SysShape { int tx, ty, tz; };
 constexpr int SYS_NSHAPES = 4;  // 2, 3: register-resident kernel, 31 x 15 x 12 / x 8 (systolic_reg.cu)
 SysShape systolic_shape(int variant);
 SysShape systolic_reg_shape(int k);
-cudaError_t systolic_reg_configure(int k, int storage);
-int systolic_reg_max_ctas_per_sm(int k, int storage);
+cudaError_t systolic_reg_configure(int k, int fmt);
+int systolic_reg_max_ctas_per_sm(int k, int fmt);
 
 struct SysLaunch {
     float *f[6];             // field arrays (elements of the storage format; FP32 for the
@@ -92,11 +101,12 @@ bool encode_shell_maps(CUtensorMap tm[3][7], void *fbase, long long fstride, con
 int systolic_reg_rows(int k);
 
 size_t systolic_smem_bytes(int variant);
-cudaError_t systolic_configure(int variant, int storage);
-int systolic_max_ctas_per_sm(int variant, int storage);
-// The shared-memory variants (0, 1) take FP32 storage only.
-cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant, int storage);
-cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int storage);
+// `fmt` is a kernel format code as for the naive scheme; the shared-memory
+// variants (0, 1) take FP32 only.
+cudaError_t systolic_configure(int variant, int fmt);
+int systolic_max_ctas_per_sm(int variant, int fmt);
+cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant, int fmt);
+cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int fmt);
 
 // Tile order for one systolic launch of up to T steps (fdtd_api.cu).
 void systolic_tile_order(const fdtd_grid &g, int variant, int T, std::vector<int> &tiles,

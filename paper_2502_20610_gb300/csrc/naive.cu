@@ -15,6 +15,7 @@
 namespace {
 
 constexpr int NAIVE_BX = 32, NAIVE_BY = 8, NAIVE_KZ = 8;
+constexpr int NAIVE_BLOCK_CELLS = 1024;
 
 template <class S>
 __global__ void __launch_bounds__(NAIVE_BX *NAIVE_BY)
@@ -82,7 +83,7 @@ naive_e_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ ey_,
         for (int q = 0; q < src.n; ++q) {
             const SrcDesc &s = src.s[q];
             if (s.idx == p && step < s.n_amp) {
-                const float a = s.amp[step];
+                const float a = S::src_amp(s.amp[step], sc.src);
                 if (s.comp == 0) ex = add_source(ex, a);
                 else if (s.comp == 1) ey = add_source(ey, a);
                 else ez = add_source(ez, a);
@@ -93,6 +94,67 @@ naive_e_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ ey_,
         ez_[p] = S::enc(ez, sc.is[2]);
         hxm = hx;
         hym = hy;
+    }
+}
+
+// Small domains (at most NAIVE_BLOCK_CELLS cells, the largest thread block):
+// one CTA, one thread per cell, runs all the steps of a call with block
+// barriers between the half-steps instead of kernel boundaries, the regime
+// of Fig. 1 in which the update needs no global synchronisation.  The data
+// change inside the launch, so loads are plain (coherent) loads; the block
+// barrier orders each half-step's stores before the next one's loads.
+template <class S>
+__global__ void __launch_bounds__(NAIVE_BLOCK_CELLS)
+naive_block_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ ey_, typename S::T *__restrict__ ez_,
+                   typename S::T *__restrict__ hx_, typename S::T *__restrict__ hy_, typename S::T *__restrict__ hz_,
+                   const float *__restrict__ ce_, int nx, int ny, int nz, int pitch, float ndt, long long step0,
+                   int nsteps, const SrcSet src, const Scales sc)
+{
+    const int q = threadIdx.x;
+    const bool own = q < nx * ny * nz;
+    const int i = own ? q % nx : 0, j = own ? (q / nx) % ny : 0, k = own ? q / (nx * ny) : 0;
+    const long long sxy = (long long)pitch * ny;
+    const long long p = i + (long long)pitch * (j + (long long)ny * k);
+    const bool ip = i + 1 < nx, jp = j + 1 < ny, kp = k + 1 < nz;
+    const float ce = own ? ce_[p] : 0.f;
+    for (int s = 0; s < nsteps; ++s) {
+        if (own) {
+            const float exc = S::dec(ex_[p], sc.s[0]), eyc = S::dec(ey_[p], sc.s[1]), ezc = S::dec(ez_[p], sc.s[2]);
+            const float exn = kp ? S::dec(ex_[p + sxy], sc.s[0]) : 0.f;
+            const float eyn = kp ? S::dec(ey_[p + sxy], sc.s[1]) : 0.f;
+            const float ez_ip = ip ? S::dec(ez_[p + 1], sc.s[2]) : 0.f;
+            const float ey_ip = ip ? S::dec(ey_[p + 1], sc.s[1]) : 0.f;
+            const float ez_jp = jp ? S::dec(ez_[p + pitch], sc.s[2]) : 0.f;
+            const float ex_jp = jp ? S::dec(ex_[p + pitch], sc.s[0]) : 0.f;
+            hx_[p] = S::enc(h_x(S::dec(hx_[p], sc.s[3]), ez_jp, ezc, eyn, eyc, ndt), sc.is[3]);
+            hy_[p] = S::enc(h_y(S::dec(hy_[p], sc.s[4]), exn, exc, ez_ip, ezc, ndt), sc.is[4]);
+            hz_[p] = S::enc(h_z(S::dec(hz_[p], sc.s[5]), ey_ip, eyc, ex_jp, exc, ndt), sc.is[5]);
+        }
+        __syncthreads();
+        if (own) {
+            const float hx = S::dec(hx_[p], sc.s[3]), hy = S::dec(hy_[p], sc.s[4]), hz = S::dec(hz_[p], sc.s[5]);
+            float ex = S::dec(ex_[p], sc.s[0]), ey = S::dec(ey_[p], sc.s[1]), ez = S::dec(ez_[p], sc.s[2]);
+            if (j > 0 && k > 0)
+                ex = e_x(ex, hz, S::dec(hz_[p - pitch], sc.s[5]), hy, S::dec(hy_[p - sxy], sc.s[4]), ce);
+            if (i > 0 && k > 0)
+                ey = e_y(ey, hx, S::dec(hx_[p - sxy], sc.s[3]), hz, S::dec(hz_[p - 1], sc.s[5]), ce);
+            if (i > 0 && j > 0)
+                ez = e_z(ez, hy, S::dec(hy_[p - 1], sc.s[4]), hx, S::dec(hx_[p - pitch], sc.s[3]), ce);
+            const long long step = step0 + s;
+            for (int qq = 0; qq < src.n; ++qq) {
+                const SrcDesc &d = src.s[qq];
+                if (d.idx == p && step < d.n_amp) {
+                    const float a = S::src_amp(d.amp[step], sc.src);
+                    if (d.comp == 0) ex = add_source(ex, a);
+                    else if (d.comp == 1) ey = add_source(ey, a);
+                    else ez = add_source(ez, a);
+                }
+            }
+            ex_[p] = S::enc(ex, sc.is[0]);
+            ey_[p] = S::enc(ey, sc.is[1]);
+            ez_[p] = S::enc(ez, sc.is[2]);
+        }
+        __syncthreads();
     }
 }
 
@@ -122,20 +184,36 @@ cudaError_t launch_e(void *const f[6], const float *ce, int nx, int ny, int nz, 
     return cudaGetLastError();
 }
 
-} // namespace
-
-cudaError_t launch_naive_h(void *const f[6], int storage, int nx, int ny, int nz, int pitch, float neg_dt,
-                           const Scales &sc, cudaStream_t st)
+template <class S>
+cudaError_t launch_block(void *const f[6], const float *ce, int nx, int ny, int nz, int pitch, float neg_dt,
+                         long long step0, int nsteps, const SrcSet &src, const Scales &sc, cudaStream_t st)
 {
-    if (storage == FDTD_STORAGE_F16) return launch_h<StoreF16>(f, nx, ny, nz, pitch, neg_dt, sc, st);
-    if (storage == FDTD_STORAGE_BF16) return launch_h<StoreBF16>(f, nx, ny, nz, pitch, neg_dt, sc, st);
-    return launch_h<StoreF32>(f, nx, ny, nz, pitch, neg_dt, sc, st);
+    using T = typename S::T;
+    const int threads = (nx * ny * nz + 31) / 32 * 32;
+    naive_block_kernel<S><<<1, threads, 0, st>>>((T *)f[0], (T *)f[1], (T *)f[2], (T *)f[3], (T *)f[4], (T *)f[5],
+                                                  ce, nx, ny, nz, pitch, neg_dt, step0, nsteps, src, sc);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_naive_e(void *const f[6], int storage, const float *ce, int nx, int ny, int nz, int pitch,
+} // namespace
+
+int naive_block_max_cells() { return NAIVE_BLOCK_CELLS; }
+
+cudaError_t launch_naive_block(void *const f[6], int fmt, const float *ce, int nx, int ny, int nz, int pitch,
+                               float neg_dt, long long step0, int nsteps, const SrcSet &src, const Scales &sc,
+                               cudaStream_t st)
+{
+    DISPATCH_FORMAT(fmt, S, launch_block<S>(f, ce, nx, ny, nz, pitch, neg_dt, step0, nsteps, src, sc, st));
+}
+
+cudaError_t launch_naive_h(void *const f[6], int fmt, int nx, int ny, int nz, int pitch, float neg_dt,
+                           const Scales &sc, cudaStream_t st)
+{
+    DISPATCH_FORMAT(fmt, S, launch_h<S>(f, nx, ny, nz, pitch, neg_dt, sc, st));
+}
+
+cudaError_t launch_naive_e(void *const f[6], int fmt, const float *ce, int nx, int ny, int nz, int pitch,
                            long long step, const SrcSet &src, const Scales &sc, cudaStream_t st)
 {
-    if (storage == FDTD_STORAGE_F16) return launch_e<StoreF16>(f, ce, nx, ny, nz, pitch, step, src, sc, st);
-    if (storage == FDTD_STORAGE_BF16) return launch_e<StoreBF16>(f, ce, nx, ny, nz, pitch, step, src, sc, st);
-    return launch_e<StoreF32>(f, ce, nx, ny, nz, pitch, step, src, sc, st);
+    DISPATCH_FORMAT(fmt, S, launch_e<S>(f, ce, nx, ny, nz, pitch, step, src, sc, st));
 }

@@ -128,6 +128,7 @@ extern "C" fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *
     p.fbase = d_fields;
     p.fstride = (long long)n;
     for (int c = 0; c < 6; ++c) p.sc.s[c] = p.sc.is[c] = 1.f;  // FP32 storage
+    p.sc.src = 1.f;
     p.gx = gx;
     p.gy = gy;
     p.gz = gz;

@@ -40,6 +40,8 @@
 #include "sys_common.cuh"
 #include "yee_cell.cuh"
 
+#include <type_traits>
+
 namespace {
 
 using namespace sysc;
@@ -407,22 +409,36 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 const int wm = (w - 1) & (R::RY - 1);
                 const int src = (lane - 1) & 31;
                 const bool ux = py > 0, uy = px > 0, uz = px > 0 && py > 0;
+                auto e_pass = [&](auto round) {
 #pragma unroll
-                for (int i = NR - 1; i >= 1; --i) {
-                    const float hz_xm = shfl_from(hz[i], src);
-                    const float hy_xm = shfl_from(hy[i], src);
-                    const float hx_ym = XHx[(wm * NZ + (i - 1)) * 32 + lane];
-                    const float hz_ym = XHz[(wm * NZ + (i - 1)) * 32 + lane];
-                    const float c = CEs[(w * CR + ((bz + i - 1) & (CR - 1))) * 32 + lane];
-                    const float nex = e_x(ex[i - 1], hz[i], hz_ym, hy[i], hy[i - 1], c);
-                    const float ney = e_y(ey[i - 1], hx[i], hx[i - 1], hz[i], hz_xm, c);
-                    const float nez = e_z(ez[i - 1], hy[i], hy_xm, hx[i], hx_ym, c);
-                    const bool in = colin && i >= i_lo && i < i_hi;
-                    const bool kz = bz + i - 1 > 0;
-                    ex[i] = (in && ux && kz) ? (srcthr ? nex : RND(nex, 0)) : ex[i - 1];
-                    ey[i] = (in && uy && kz) ? (srcthr ? ney : RND(ney, 1)) : ey[i - 1];
-                    ez[i] = (in && uz) ? (srcthr ? nez : RND(nez, 2)) : ez[i - 1];
-                }
+                    for (int i = NR - 1; i >= 1; --i) {
+                        const float hz_xm = shfl_from(hz[i], src);
+                        const float hy_xm = shfl_from(hy[i], src);
+                        const float hx_ym = XHx[(wm * NZ + (i - 1)) * 32 + lane];
+                        const float hz_ym = XHz[(wm * NZ + (i - 1)) * 32 + lane];
+                        const float c = CEs[(w * CR + ((bz + i - 1) & (CR - 1))) * 32 + lane];
+                        float nex = e_x(ex[i - 1], hz[i], hz_ym, hy[i], hy[i - 1], c);
+                        float ney = e_y(ey[i - 1], hx[i], hx[i - 1], hz[i], hz_xm, c);
+                        float nez = e_z(ez[i - 1], hy[i], hy_xm, hx[i], hx_ym, c);
+                        if (decltype(round)::value) {
+                            nex = RND(nex, 0);
+                            ney = RND(ney, 1);
+                            nez = RND(nez, 2);
+                        }
+                        const bool in = colin && i >= i_lo && i < i_hi;
+                        const bool kz = bz + i - 1 > 0;
+                        ex[i] = (in && ux && kz) ? nex : ex[i - 1];
+                        ey[i] = (in && uy && kz) ? ney : ey[i - 1];
+                        ez[i] = (in && uz) ? nez : ez[i - 1];
+                    }
+                };
+                // 16-bit storage rounds each new E value here, except in the
+                // (rare) thread that adds a point source this step: it rounds
+                // after the source, below
+                if (S::narrow && !srcthr)
+                    e_pass(std::integral_constant<bool, true>());
+                else
+                    e_pass(std::integral_constant<bool, false>());
                 if (xbox) {  // row -1 takes the lower z shell's E (level t)
                     const int o = (dy + 1) * SW + (px - x0);
                     ex[0] = S::dec(ZST[0 * R::ZB + o], SC(0));
@@ -444,7 +460,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 const SrcDesc &s = P.src.s[q];
                 if (step < s.n_amp && s.i >= bx && s.i < bx + TX && s.j >= by && s.j < by + TY &&
                     s.k >= bz && s.k < bz + TZ && lane == (s.i & 31) && w == (s.j & (R::RY - 1))) {
-                    const float a = s.amp[step];
+                    const float a = S::src_amp(s.amp[step], P.sc.src);
                     const int ri = s.k - bz + 1;
 #pragma unroll
                     for (int i = 1; i < NR; ++i) {
@@ -553,26 +569,14 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #undef RND
 #undef STORE6
 
-// 31 x 15 x 12 and 31 x 15 x 8 tiles, each for the three storage formats
+// 31 x 15 x 12 and 31 x 15 x 8 tiles, each for every kernel format
 template <int NZ>
 struct RegShape {
-    static cudaError_t configure(int storage)
+    static cudaError_t configure(int fmt) { DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S>>()); }
+    static int per_sm(int fmt) { DISPATCH_FORMAT(fmt, S, occ<RegTile<NZ, S>>()); }
+    static cudaError_t launch(const SysLaunch &p, int grid, cudaStream_t st, int fmt)
     {
-        if (storage == FDTD_STORAGE_F16) return set<RegTile<NZ, StoreF16>>();
-        if (storage == FDTD_STORAGE_BF16) return set<RegTile<NZ, StoreBF16>>();
-        return set<RegTile<NZ, StoreF32>>();
-    }
-    static int per_sm(int storage)
-    {
-        if (storage == FDTD_STORAGE_F16) return occ<RegTile<NZ, StoreF16>>();
-        if (storage == FDTD_STORAGE_BF16) return occ<RegTile<NZ, StoreBF16>>();
-        return occ<RegTile<NZ, StoreF32>>();
-    }
-    static cudaError_t launch(const SysLaunch &p, int grid, cudaStream_t st, int storage)
-    {
-        if (storage == FDTD_STORAGE_F16) return go<RegTile<NZ, StoreF16>>(p, grid, st);
-        if (storage == FDTD_STORAGE_BF16) return go<RegTile<NZ, StoreBF16>>(p, grid, st);
-        return go<RegTile<NZ, StoreF32>>(p, grid, st);
+        DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S>>(p, grid, st));
     }
     template <class R>
     static cudaError_t set()
@@ -606,14 +610,11 @@ int systolic_reg_rows(int k) { return (k == 0 ? 12 : 8) + 1; }
 
 SysShape systolic_reg_shape(int k) { return SysShape{31, 15, k == 0 ? 12 : 8}; }
 
-cudaError_t systolic_reg_configure(int k, int storage)
-{
-    return k == 0 ? RegA::configure(storage) : RegB::configure(storage);
-}
+cudaError_t systolic_reg_configure(int k, int fmt) { return k == 0 ? RegA::configure(fmt) : RegB::configure(fmt); }
 
-int systolic_reg_max_ctas_per_sm(int k, int storage) { return k == 0 ? RegA::per_sm(storage) : RegB::per_sm(storage); }
+int systolic_reg_max_ctas_per_sm(int k, int fmt) { return k == 0 ? RegA::per_sm(fmt) : RegB::per_sm(fmt); }
 
-cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int storage)
+cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int fmt)
 {
-    return k == 0 ? RegA::launch(p, grid, st, storage) : RegB::launch(p, grid, st, storage);
+    return k == 0 ? RegA::launch(p, grid, st, fmt) : RegB::launch(p, grid, st, fmt);
 }

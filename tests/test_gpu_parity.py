@@ -168,3 +168,20 @@ def test_bad_arguments_through_the_abi(cuda_device):
     sim.close()
     with pytest.raises(fdtd.FdtdError):
         fdtd.Sim(shape, -np.ones(shape), DT)  # eps must be positive
+
+
+@pytest.mark.parametrize("shape", [(8, 9, 10), (4, 16, 16), (1, 1, 1), (2, 31, 16)])
+def test_naive_single_block_path(cuda_device, shape):
+    # grids of at most 1024 cells run the naive schedule in one CTA per call
+    # (block barriers instead of launch boundaries): same results bit for bit
+    eps = wl.random_eps(shape, 12)
+    f0 = wl.random_fields(shape, 12, zero_pec_walls=False)
+    nz, ny, nx = shape
+    src = [(1, nx // 2, ny // 2, nz // 2, wl.sine_source(40, DT))]
+    a, nl = run_gpu(shape, eps, f0, 40, "naive", sources=src, split=[13, 27])
+    assert nl == 2
+    b, _ = run_gpu(shape, eps, f0, 40, "systolic", sources=src)
+    assert bits_equal(a, b)
+    ref = oracle_run(shape, eps, f0, 40, sources=src, quantize=True)
+    err = rel_l2_per_field(a.numpy(), ref)
+    assert max(err.values()) < TOL, err

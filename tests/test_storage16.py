@@ -143,10 +143,13 @@ def _oracle16(shape, eps, f0, steps, storage, scales, sources=()):
 @pytest.mark.parametrize("shape,steps", [((17, 17, 17), 29), ((47, 65, 33), 23), ((5, 3, 100), 12),
                                          ((40, 1, 1), 9), ((30, 31, 70), 40)])
 @pytest.mark.parametrize("tile", REG_TILES)
-def test_16bit_systolic_bitexact_naive(cuda_device, storage, shape, steps, tile):
+@pytest.mark.parametrize("scales", [None, (0.5,) * 6, (1.0, 0.5, 2.0, 1.0, 0.25, 4.0)],
+                         ids=["unit", "uniform", "per-component"])
+def test_16bit_systolic_bitexact_naive(cuda_device, storage, shape, steps, tile, scales):
+    # equal scales step the stored values directly, unequal ones decode and
+    # re-encode per component: both kernel forms are covered
     eps = wl.random_eps(shape, 5)
     f0 = wl.random_fields(shape, 5, zero_pec_walls=False)
-    scales = [1.0, 0.5, 2.0, 1.0, 0.25, 4.0]
     nz, ny, nx = shape
     src = [(2, nx // 2, ny // 2, nz // 2, wl.sine_source(steps, DT)),
            (0, nx - 1, ny - 1, nz - 1, wl.sine_source(steps, DT, 7.0))]
@@ -158,7 +161,8 @@ def test_16bit_systolic_bitexact_naive(cuda_device, storage, shape, steps, tile)
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
-def test_16bit_first_steps_match_oracle_emulation(cuda_device, storage):
+@pytest.mark.parametrize("scales", [(0.5,) * 6, (1.0, 2.0, 0.5, 1.0, 1.0, 0.25)], ids=["uniform", "per-component"])
+def test_16bit_first_steps_match_oracle_emulation(cuda_device, storage, scales):
     # FP32 and FP64 arithmetic round to the same 16-bit value unless the exact
     # result lies within ~1e-7 (relative) of a rounding boundary.  After one
     # step: every H value (computed from identical E^0) equals the emulation
@@ -168,7 +172,7 @@ def test_16bit_first_steps_match_oracle_emulation(cuda_device, storage):
     shape = (24, 28, 40)
     eps = wl.random_eps(shape, 6)
     f0 = wl.random_fields(shape, 6)
-    scales = np.array([1.0, 2.0, 0.5, 1.0, 1.0, 0.25])
+    scales = np.array(scales)
     src = [(2, 20, 14, 12, wl.sine_source(3, DT))]
     u = UNIT[storage]
     floor = scales[:, None, None, None] * (2.0 ** -24 if storage == "f16" else 0.0)  # binary16 subnormal step
