@@ -49,6 +49,9 @@ def _load():
     lib.oracle_round_to_format.restype = ctypes.c_double
     lib.oracle_round_to_format.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.oracle_set_storage.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, D]
+    lib.oracle_set_eps_sigma.argtypes = [P, D, D, ctypes.c_int]
+    lib.oracle_graded_sigma.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, ctypes.c_int, D]
+    lib.oracle_get_ca.argtypes = [P, D]
     _lib = lib
     return lib
 
@@ -65,6 +68,16 @@ def round_to_format(x, fmt):
     x = np.asarray(x, dtype=np.float64)
     f = lib.oracle_round_to_format
     return np.array([f(float(v), p, emin, emax) for v in x.ravel()], dtype=np.float64).reshape(x.shape)
+
+
+def graded_sigma(shape_zyx, thickness, sigma_max, order):
+    """Graded conductivity sigma_max * sum_a (depth_a / L)^m of the absorbing
+    layer (oracle's own profile routine), as an (nz, ny, nx) float64 array."""
+    lib = _load()
+    nz, ny, nx = (int(s) for s in shape_zyx)
+    out = np.empty((nz, ny, nx), dtype=np.float64)
+    lib.oracle_graded_sigma(nx, ny, nz, int(thickness), float(sigma_max), int(order), _dptr(out))
+    return out
 
 
 def _dptr(a):
@@ -108,6 +121,18 @@ class YeeOracle:
     def set_eps(self, eps, quantize_ce_f32=False):
         e = self._arr(eps)
         self._lib.oracle_set_eps(self._h, _dptr(e), 1 if quantize_ce_f32 else 0)
+
+    def set_eps_sigma(self, eps, sigma, quantize_f32=False):
+        """Per-cell eps and conductivity: the E half-step becomes
+        E <- ca E + cb curl H (cb also scales the sources)."""
+        e = self._arr(eps)
+        sg = self._arr(sigma)
+        self._lib.oracle_set_eps_sigma(self._h, _dptr(e), _dptr(sg), 1 if quantize_f32 else 0)
+
+    def ca(self):
+        out = np.empty(self.shape, dtype=np.float64)
+        self._lib.oracle_get_ca(self._h, _dptr(out))
+        return out
 
     def set_fields(self, fields):
         """fields: sequence of 6 arrays (Ex, Ey, Ez, Hx, Hy, Hz) or a (6, nz, ny, nx) array."""

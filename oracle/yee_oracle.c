@@ -17,6 +17,16 @@
  *   ce = dt / eps per cell (Eq. 1 prints the vacuum case dt/dy; the paper's
  *   implementation carries a per-cell permittivity structure field, Sec. 4).
  *
+ * Conductivity (the lossy structure field of Sec. 4, used for absorbing
+ *   layers): with sigma > 0 in a cell, the E half-step is the time-centred
+ *   discretisation of eps dE/dt + sigma E = curl H - J,
+ *       E^{n+1} = ca * E^n + cb * (curl_b H^{n+1/2} - J),
+ *       ca = (1 - sigma dt / (2 eps)) / (1 + sigma dt / (2 eps)),
+ *       cb = (dt / eps) / (1 + sigma dt / (2 eps)),
+ *   which is the lossless update when sigma = 0.  The graded absorber sets
+ *   sigma = sigma_max * sum_a (depth_a / L)^m over a layer of L cells at
+ *   every wall, depth_a = L - i for i < L, i - (N - 1 - L) for i >= N - L.
+ *
  * Grid convention: arrays of nx*ny*nz doubles, index i + nx*(j + ny*k).
  *   Cell (i,j,k) holds Ex(i+1/2,j,k), Ey(i,j+1/2,k), Ez(i,j,k+1/2),
  *   Hx(i,j+1/2,k+1/2), Hy(i+1/2,j,k+1/2), Hz(i+1/2,j+1/2,k).
@@ -56,7 +66,8 @@ typedef struct {
     int nx, ny, nz, periodic;
     double dt;
     double *f[6];  /* Ex Ey Ez Hx Hy Hz */
-    double *ce;    /* per-cell E coefficient */
+    double *ce;    /* per-cell E coefficient cb (dt/eps when lossless) */
+    double *ca;    /* per-cell E decay ca, NULL when lossless */
     long step;
     int nsrc;
     or_source src[OR_MAX_SOURCES];
@@ -85,6 +96,7 @@ void oracle_destroy(yee_oracle *o)
     if (!o) return;
     for (int c = 0; c < 6; ++c) free(o->f[c]);
     free(o->ce);
+    free(o->ca);
     for (int s = 0; s < o->nsrc; ++s) free(o->src[s].J);
     free(o);
 }
@@ -98,6 +110,46 @@ void oracle_set_eps(yee_oracle *o, const double *eps, int quantize_f32)
         double c = o->dt / eps[p];
         o->ce[p] = quantize_f32 ? (double)(float)c : c;
     }
+}
+
+/* eps and conductivity sigma per cell: ca and cb as above; quantize_f32 != 0
+ * rounds ca and cb to float once (the GPU's coefficients). */
+void oracle_set_eps_sigma(yee_oracle *o, const double *eps, const double *sigma, int quantize_f32)
+{
+    long n = ncell(o);
+    if (!o->ca) o->ca = (double *)malloc(sizeof(double) * (size_t)n);
+    for (long p = 0; p < n; ++p) {
+        double h = sigma[p] * o->dt / (2.0 * eps[p]);
+        double a = (1.0 - h) / (1.0 + h), b = (o->dt / eps[p]) / (1.0 + h);
+        if (o->mutation == 6) a = (1.0 + h) / (1.0 - h); /* planted: loss with the wrong sign */
+        o->ca[p] = quantize_f32 ? (double)(float)a : a;
+        o->ce[p] = quantize_f32 ? (double)(float)b : b;
+    }
+}
+
+/* The graded profile: sigma_max * sum over axes of (depth / L)^m. */
+void oracle_graded_sigma(int nx, int ny, int nz, int L, double sigma_max, int m, double *sigma)
+{
+    int n[3] = {nx, ny, nz};
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int idx[3] = {i, j, k};
+                double s = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    int d = 0;
+                    if (idx[a] < L) d = L - idx[a];
+                    else if (idx[a] >= n[a] - L) d = idx[a] - (n[a] - 1 - L);
+                    if (d > 0) s += pow((double)d / L, m);
+                }
+                sigma[i + (long)nx * (j + (long)ny * k)] = sigma_max * s;
+            }
+}
+
+void oracle_get_ca(const yee_oracle *o, double *dst)
+{
+    long n = ncell(o);
+    for (long p = 0; p < n; ++p) dst[p] = o->ca ? o->ca[p] : 1.0;
 }
 
 void oracle_set_field(yee_oracle *o, int comp, const double *src)
@@ -244,9 +296,10 @@ static void half_step_e(yee_oracle *o, double **eout)
                 long p = i + (long)nx * (j + (long)ny * k);
                 double c[3];
                 curl_h(o, i, j, k, c);
+                double decay = o->ca ? o->ca[p] : 1.0;
                 for (int a = 0; a < 3; ++a)
                     eout[a][p] = pec_fixed(o, a, i, j, k) ? o->f[EX + a][p]
-                                                          : o->f[EX + a][p] + o->ce[p] * c[a];
+                                                          : decay * o->f[EX + a][p] + o->ce[p] * c[a];
             }
 }
 
@@ -278,8 +331,18 @@ int oracle_step(yee_oracle *o, long n)
     return 0;
 }
 
-/* Q^n = sum eps_eff |E^n|^2 + sum H^{n-1/2} . H^{n+1/2}, eps_eff = dt/ce.
- * Conserved exactly by the leapfrog in a lossless, source-free box. */
+/* Effective permittivity of cell p for the coefficients in use: from
+ * ca = (eps - g)/(eps + g), cb = dt/(eps + g) with g = sigma dt / 2,
+ * eps = (dt/cb)(1 + ca)/2 and g = (dt/cb)(1 - ca)/2 (eps = dt/ce when lossless). */
+static double eps_eff(const yee_oracle *o, long p)
+{
+    double a = o->ca ? o->ca[p] : 1.0;
+    return o->dt / o->ce[p] * (1.0 + a) * 0.5;
+}
+
+/* Q^n = sum eps_eff |E^n|^2 + sum H^{n-1/2} . H^{n+1/2}.
+ * Conserved exactly by the leapfrog in a lossless, source-free box; with
+ * conductivity, Q^{n+1} - Q^n = -sum g |E^{n+1} + E^n|^2 exactly. */
 double oracle_energy(const yee_oracle *o)
 {
     const int nx = o->nx, ny = o->ny, nz = o->nz;
@@ -289,7 +352,7 @@ double oracle_energy(const yee_oracle *o)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 long p = i + (long)nx * (j + (long)ny * k);
-                double w = o->dt / o->ce[p];
+                double w = eps_eff(o, p);
                 double c[3];
                 curl_e(o, i, j, k, c);
                 for (int a = 0; a < 3; ++a) {
@@ -314,12 +377,12 @@ void oracle_div(const yee_oracle *o, double *div_e, double *div_h)
                 double d = 0.0;
                 int ii[3] = {i - 1, i, i}, jj[3] = {j, j - 1, j}, kk[3] = {k, k, k - 1};
                 for (int a = 0; a < 3; ++a) {
-                    double w0 = o->dt / o->ce[p];
+                    double w0 = eps_eff(o, p);
                     double lo = at(o, EX + a, ii[a], jj[a], kk[a]);
                     double wlo = 0.0;
                     if (o->periodic || (ii[a] >= 0 && jj[a] >= 0 && kk[a] >= 0)) {
                         int i2 = (ii[a] + nx) % nx, j2 = (jj[a] + ny) % ny, k2 = (kk[a] + nz) % nz;
-                        wlo = o->dt / o->ce[i2 + (long)nx * (j2 + (long)ny * k2)];
+                        wlo = eps_eff(o, i2 + (long)nx * (j2 + (long)ny * k2));
                     }
                     d += w0 * o->f[EX + a][p] - wlo * lo;
                 }
