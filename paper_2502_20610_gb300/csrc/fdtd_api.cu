@@ -23,7 +23,7 @@ constexpr unsigned EPOCH_LIMIT = 1u << 30;
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-    size_t fields[6], ce, stage, src, progress, tiles, ctrl, total;
+    size_t fields[6], ce, ca, stage, src, progress, tiles, ctrl, total;
     int eb;     // bytes per stored field value (4 FP32, 2 FP16/BF16)
     int pitch;  // elements per x row in device memory (nx rounded up to 16 bytes)
     int variant, tx, ty, tz;  // systolic tile shape
@@ -51,7 +51,7 @@ int pick_variant(const fdtd_coeffs &c)
 //   6 field arrays in the storage format, the FP32 coefficient dt/eps, (16-bit
 //   storage) one dense FP32 component for host transfers, the source tables,
 //   and (systolic) one progress flag per skewed tile plus the tile order.
-bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, Layout &L)
+bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, const fdtd_boundary &b, Layout &L)
 {
     // rows padded to a 16-byte multiple, so every row starts 16-byte aligned
     // (a requirement of bulk tensor copies); the padding cells are never read
@@ -66,6 +66,8 @@ bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, Layout &L)
     }
     L.ce = off;
     off = align_up(off + sizeof(float) * (size_t)n);
+    L.ca = off;  // E decay of conducting cells (absorber)
+    if (b.kind == FDTD_BOUNDARY_GRADED_ABSORBER) off = align_up(off + sizeof(float) * (size_t)n);
     L.stage = off;
     if (c.storage != FDTD_STORAGE_F32) off = align_up(off + sizeof(float) * (size_t)g.nx * g.ny * g.nz);
     L.source_steps = c.max_source_steps > 0 ? c.max_source_steps : DEFAULT_SOURCE_STEPS;
@@ -125,8 +127,32 @@ fdtd_status check_args(const fdtd_grid *g, const fdtd_coeffs *c, const fdtd_boun
     for (int a = 0; a < 3; ++a)
         if (c->cluster[a] > 1) return FDTD_ERR_UNSUPPORTED;
     if (b->kind < FDTD_BOUNDARY_PEC || b->kind > FDTD_BOUNDARY_LEARNED) return FDTD_ERR_INVALID_ARG;
-    if (b->kind != FDTD_BOUNDARY_PEC) return FDTD_ERR_UNSUPPORTED;
+    if (b->kind == FDTD_BOUNDARY_GRADED_ABSORBER) {
+        if (b->thickness < 1 || !(b->sigma_max >= 0.0) || !std::isfinite(b->sigma_max) || b->poly_order < 0 ||
+            b->poly_order > 16)
+            return FDTD_ERR_INVALID_ARG;
+        // the register kernel's 31 x 15 x 12 tile is the one built with the lossy update
+        if (c->scheme == FDTD_SCHEME_SYSTOLIC && pick_variant(*c) != 2) return FDTD_ERR_UNSUPPORTED;
+    }
+    if (b->kind == FDTD_BOUNDARY_LEARNED) return FDTD_ERR_UNSUPPORTED;
     return FDTD_OK;
+}
+
+// Graded conductivity of cell (i,j,k): sigma_max * sum over the axes of
+// (depth / L)^m, depth = L - i inside the low layer (i < L), i - (N-1-L) inside
+// the high one (i >= N - L), 0 elsewhere.
+double graded_sigma_at(const fdtd_grid &g, const fdtd_boundary &b, int i, int j, int k)
+{
+    const int idx[3] = {i, j, k}, n[3] = {g.nx, g.ny, g.nz};
+    const int L = b.thickness;
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        int d = 0;
+        if (idx[a] < L) d = L - idx[a];
+        else if (idx[a] >= n[a] - L) d = idx[a] - (n[a] - 1 - L);
+        if (d > 0) s += std::pow((double)d / L, b.poly_order);
+    }
+    return b.sigma_max * s;
 }
 
 // Skewed-tile schedule.  Tile (I,J,K) covers sigma in [A, A+n) with
@@ -204,21 +230,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-bool encode_shell_maps(CUtensorMap tm[3][7], void *fbase, long long fstride, const float *ce, int storage,
-                       int nx, int ny, int nz, int pitch, int nr)
+bool encode_shell_maps(CUtensorMap tm[3][8], void *fbase, long long fstride, const float *ce, const float *ca,
+                       int storage, int nx, int ny, int nz, int pitch, int nr)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || fstride <= 0) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint32_t estr[3] = {1, 1, 1};
-    for (int a = 0; a < 7; ++a) {
-        // array 6 is dt/eps (FP32); the fields use the storage element
+    std::memset(tm, 0, sizeof(CUtensorMap) * 3 * 8);
+    for (int a = 0; a < (ca ? 8 : 7); ++a) {
+        // arrays 6, 7 are dt/eps (cb) and ca (FP32); the fields use the storage element
         const int eb = a < 6 ? storage_bytes(storage) : 4;
         const cuuint32_t xa = 16u / (cuuint32_t)eb, sw = 32u + xa;
         const cuuint64_t strides[2] = {(cuuint64_t)pitch * eb, (cuuint64_t)pitch * (cuuint64_t)ny * eb};
         // lower z shell {sw,16,1}, lower y shell {sw,1,nr}, lower x shell {xa,16,nr}
         const cuuint32_t box[3][3] = {{sw, 16, 1}, {sw, 1, (cuuint32_t)nr}, {xa, 16, (cuuint32_t)nr}};
-        void *base = a < 6 ? (void *)((char *)fbase + (size_t)a * (size_t)fstride * eb) : (void *)ce;
+        void *base = a < 6 ? (void *)((char *)fbase + (size_t)a * (size_t)fstride * eb)
+                           : (void *)(a == 6 ? ce : ca);
         const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
         for (int s = 0; s < 3; ++s) {
             CUresult r = enc(&tm[s][a], dt, 3, base, dims, strides, box[s], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -244,8 +272,10 @@ void systolic_tile_order(const fdtd_grid &g, int variant, int T, std::vector<int
     c.tile[0] = sh.tx;
     c.tile[1] = sh.ty;
     c.tile[2] = sh.tz;
+    fdtd_boundary b;
+    std::memset(&b, 0, sizeof(b));
     Layout L;
-    make_layout(g, c, L);
+    make_layout(g, c, b, L);
     build_tiles(g, L, 0, 0u, tiles, count_le);
     gx = L.gx;
     gy = L.gy;
@@ -261,6 +291,7 @@ struct fdtd_sim {
     Layout L;
     void *f[6];
     float *ce;
+    float *ca;     // E decay per cell (absorber), else null
     float *stage;  // dense FP32 component (16-bit storage), else null
     Scales sc;
     int fmt;       // kernel format (storage.cuh): the storage, or its uniform-scale variant
@@ -278,7 +309,7 @@ struct fdtd_sim {
     int dbg_kind;
     long long dbg_ticket, dbg_param, dbg_param2;
     bool failed;
-    CUtensorMap tm[3][7];  // shell maps of the register kernel
+    CUtensorMap tm[3][8];  // shell maps of the register kernel
 };
 
 namespace {
@@ -341,7 +372,7 @@ fdtd_status fdtd_workspace_size(const fdtd_grid *grid, const fdtd_coeffs *coeffs
     fdtd_status s = check_args(grid, coeffs, boundary);
     if (s != FDTD_OK) return s;
     Layout L;
-    if (!make_layout(*grid, *coeffs, L)) return FDTD_ERR_UNSUPPORTED;
+    if (!make_layout(*grid, *coeffs, *boundary, L)) return FDTD_ERR_UNSUPPORTED;
     *bytes = L.total;
     return FDTD_OK;
 }
@@ -356,7 +387,7 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     if (s != FDTD_OK) return s;
     if (!eps || !d_workspace || ((uintptr_t)d_workspace % ALIGN) != 0) return FDTD_ERR_INVALID_ARG;
     Layout L;
-    if (!make_layout(*grid, *coeffs, L)) return FDTD_ERR_UNSUPPORTED;
+    if (!make_layout(*grid, *coeffs, *boundary, L)) return FDTD_ERR_UNSUPPORTED;
     if (ws_bytes < L.total) return FDTD_ERR_OOM;
     const long long n = (long long)grid->nx * grid->ny * grid->nz;
     for (long long p = 0; p < n; ++p)
@@ -372,6 +403,7 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     h->L = L;
     for (int k = 0; k < 6; ++k) h->f[k] = h->ws + L.fields[k];
     h->ce = (float *)(h->ws + L.ce);
+    h->ca = boundary->kind == FDTD_BOUNDARY_GRADED_ABSORBER ? (float *)(h->ws + L.ca) : nullptr;
     h->stage = coeffs->storage != FDTD_STORAGE_F32 ? (float *)(h->ws + L.stage) : nullptr;
     for (int k = 0; k < 6; ++k) {
         const float sk = coeffs->storage != FDTD_STORAGE_F32 && coeffs->field_scale[k] != 0.f ? coeffs->field_scale[k]
@@ -405,13 +437,31 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
         delete h;
         return st;
     };
-    // E coefficient: dt/eps in FP64, rounded to FP32 once per cell
-    std::vector<float> ce((size_t)n);
-    for (long long p = 0; p < n; ++p) ce[(size_t)p] = (float)(coeffs->dt / eps[p]);
+    // E coefficients, formed in FP64 and rounded to FP32 once per cell:
+    // dt/eps, or for conducting cells (absorber, sigma > 0) the time-centred
+    // form cb = (dt/eps)/(1 + g), ca = (1 - g)/(1 + g), g = sigma dt/(2 eps)
+    std::vector<float> ce((size_t)n), ca(h->ca ? (size_t)n : 0);
+    for (int k = 0; k < grid->nz; ++k)
+        for (int j = 0; j < grid->ny; ++j)
+            for (int i = 0; i < grid->nx; ++i) {
+                const size_t p = (size_t)i + (size_t)grid->nx * ((size_t)j + (size_t)grid->ny * k);
+                if (h->ca) {
+                    const double g = graded_sigma_at(*grid, *boundary, i, j, k) * coeffs->dt / (2.0 * eps[p]);
+                    ce[p] = (float)((coeffs->dt / eps[p]) / (1.0 + g));
+                    ca[p] = (float)((1.0 - g) / (1.0 + g));
+                } else {
+                    ce[p] = (float)(coeffs->dt / eps[p]);
+                }
+            }
     const size_t padded = (size_t)L.pitch * grid->ny * grid->nz;
     cudaError_t e = cudaMemsetAsync(h->ce, 0, sizeof(float) * padded, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(h->ce, sizeof(float) * L.pitch, ce.data(), sizeof(float) * grid->nx,
+                              sizeof(float) * grid->nx, (size_t)grid->ny * grid->nz, cudaMemcpyHostToDevice,
+                              h->stream);
+    if (e == cudaSuccess && h->ca) e = cudaMemsetAsync(h->ca, 0, sizeof(float) * padded, h->stream);
+    if (e == cudaSuccess && h->ca)
+        e = cudaMemcpy2DAsync(h->ca, sizeof(float) * L.pitch, ca.data(), sizeof(float) * grid->nx,
                               sizeof(float) * grid->nx, (size_t)grid->ny * grid->nz, cudaMemcpyHostToDevice,
                               h->stream);
     for (int k = 0; k < 6 && e == cudaSuccess; ++k)  // all-zero bits are +0 in every format
@@ -423,19 +473,19 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     if (e != cudaSuccess) return fail(cuda_status(e));
 
     if (coeffs->scheme == FDTD_SCHEME_SYSTOLIC) {
-        e = systolic_configure(L.variant, h->fmt);
+        e = systolic_configure(L.variant, h->fmt, h->ca != nullptr);
         if (e != cudaSuccess) return fail(cuda_status(e));
         int dev = 0, sms = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return fail(cuda_status(e));
-        const int per_sm = systolic_max_ctas_per_sm(L.variant, h->fmt);
+        const int per_sm = systolic_max_ctas_per_sm(L.variant, h->fmt, h->ca != nullptr);
         if (per_sm < 1) return fail(FDTD_ERR_UNSUPPORTED);
         h->max_ctas = sms * per_sm;
         if (L.variant >= 2) {
             const long long fstride = (long long)(L.fields[1] - L.fields[0]) / L.eb;
-            if (!encode_shell_maps(h->tm, h->f[0], fstride, h->ce, coeffs->storage, grid->nx, grid->ny, grid->nz,
-                                   L.pitch, systolic_reg_rows(L.variant - 2)))
+            if (!encode_shell_maps(h->tm, h->f[0], fstride, h->ce, h->ca, coeffs->storage, grid->nx, grid->ny,
+                                   grid->nz, L.pitch, systolic_reg_rows(L.variant - 2)))
                 return fail(FDTD_ERR_UNSUPPORTED);
         }
         fdtd_status st = upload_tiles(h, 0, 0);
@@ -456,7 +506,9 @@ fdtd_status fdtd_add_source(fdtd_handle h, int32_t component, int32_t i, int32_t
     if (h->src.n >= FDTD_MAX_SOURCES) return FDTD_ERR_STATE;
     const long long dense = i + (long long)h->g.nx * (j + (long long)h->g.ny * k);
     const long long idx = i + (long long)h->L.pitch * (j + (long long)h->g.ny * k);
-    const double c = h->c.dt / h->eps_host[(size_t)dense];
+    // the cell's cb (dt/eps unless it conducts)
+    double c = h->c.dt / h->eps_host[(size_t)dense];
+    if (h->ca) c /= 1.0 + graded_sigma_at(h->g, h->b, i, j, k) * h->c.dt / (2.0 * h->eps_host[(size_t)dense]);
     std::vector<float> amp((size_t)std::max<int64_t>(n_steps, 1));
     for (int64_t n = 0; n < n_steps; ++n) amp[(size_t)n] = (float)(-c * J[n]);
     float *dst = h->src_tab + (size_t)h->src.n * (size_t)h->L.source_steps;
@@ -510,7 +562,7 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         if (cells <= naive_block_max_cells()) {  // one CTA holds the domain: no global sync
             while (n > 0) {
                 const int T = (int)std::min<int64_t>(n, 1 << 20);
-                CK(launch_naive_block(h->f, h->fmt, h->ce, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->step, T,
+                CK(launch_naive_block(h->f, h->fmt, h->ce, h->ca, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->step, T,
                                       h->src, h->sc, h->stream));
                 h->launches += 1;
                 h->step += T;
@@ -520,7 +572,7 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         }
         for (int64_t s = 0; s < n; ++s) {
             CK(launch_naive_h(h->f, h->fmt, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->sc, h->stream));
-            CK(launch_naive_e(h->f, h->fmt, h->ce, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->step, h->src,
+            CK(launch_naive_e(h->f, h->fmt, h->ce, h->ca, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->step, h->src,
                               h->sc, h->stream));
             h->launches += 2;
             h->step += 1;
@@ -537,6 +589,7 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         SysLaunch p;
         for (int k = 0; k < 6; ++k) p.f[k] = (float *)h->f[k];
         p.ce = h->ce;
+        p.ca = h->ca;
         p.nx = h->g.nx;
         p.ny = h->g.ny;
         p.nz = h->g.nz;

@@ -35,16 +35,18 @@ struct SrcSet {
 // always FP32.
 cudaError_t launch_naive_h(void *const f[6], int fmt, int nx, int ny, int nz, int pitch, float neg_dt,
                            const Scales &sc, cudaStream_t st);
-cudaError_t launch_naive_e(void *const f[6], int fmt, const float *ce, int nx, int ny, int nz, int pitch,
-                           long long step, const SrcSet &src, const Scales &sc, cudaStream_t st);
+// ca: per-cell E decay of conducting cells (absorber), or null when lossless;
+// ce then holds cb.
+cudaError_t launch_naive_e(void *const f[6], int fmt, const float *ce, const float *ca, int nx, int ny, int nz,
+                           int pitch, long long step, const SrcSet &src, const Scales &sc, cudaStream_t st);
 
 // Naive scheme on a domain of at most naive_block_max_cells() cells: one
 // CTA, one thread per cell, `nsteps` steps in one launch (block barriers
 // between the half-steps).
 int naive_block_max_cells();
-cudaError_t launch_naive_block(void *const f[6], int fmt, const float *ce, int nx, int ny, int nz, int pitch,
-                               float neg_dt, long long step0, int nsteps, const SrcSet &src, const Scales &sc,
-                               cudaStream_t st);
+cudaError_t launch_naive_block(void *const f[6], int fmt, const float *ce, const float *ca, int nx, int ny, int nz,
+                               int pitch, float neg_dt, long long step0, int nsteps, const SrcSet &src,
+                               const Scales &sc, cudaStream_t st);
 
 // FP32 <-> storage conversion of one component (convert.cu): `dense` holds
 // nx*ny*nz values, `pitched` rows of `pitch` elements.
@@ -62,13 +64,14 @@ struct SysShape { int tx, ty, tz; };
 constexpr int SYS_NSHAPES = 4;  // 2, 3: register-resident kernel, 31 x 15 x 12 / x 8 (systolic_reg.cu)
 SysShape systolic_shape(int variant);
 SysShape systolic_reg_shape(int k);
-cudaError_t systolic_reg_configure(int k, int fmt);
-int systolic_reg_max_ctas_per_sm(int k, int fmt);
+cudaError_t systolic_reg_configure(int k, int fmt, bool lossy);
+int systolic_reg_max_ctas_per_sm(int k, int fmt, bool lossy);
 
 struct SysLaunch {
     float *f[6];             // field arrays (elements of the storage format; FP32 for the
                              // shared-memory kernel)
-    const float *ce;
+    const float *ce;         // dt/eps, or cb in conducting cells
+    const float *ca;         // E decay per cell (absorber), null when lossless
     int nx, ny, nz;
     int pitch;               // elements between consecutive x rows (>= nx)
     float *fbase;            // f[c] == fbase + c*fstride elements for c in 0..5 when the
@@ -87,24 +90,25 @@ struct SysLaunch {
     int dbg_kind;
     long long dbg_ticket, dbg_param, dbg_param2;
     SrcSet src;
-    // bulk-tensor (TMA) maps of the 6 fields and dt/eps, for the register
-    // kernel's shell staging: [shape][array], shapes = lower z, y, x shell
-    CUtensorMap tm[3][7];
+    // bulk-tensor (TMA) maps of the 6 fields, dt/eps (cb) and ca, for the
+    // register kernel's shell staging: [shape][array], shapes = lower z, y, x shell
+    CUtensorMap tm[3][8];
 };
 
 // Encode the 21 shell maps of the register kernel with `nr` z rows per
 // column: the six fields (storage format `storage`, at fbase + c*fstride
 // elements) and the FP32 coefficient array ce, all with rows of `pitch`
 // elements.  Returns false on failure.
-bool encode_shell_maps(CUtensorMap tm[3][7], void *fbase, long long fstride, const float *ce, int storage,
-                       int nx, int ny, int nz, int pitch, int nr);
+bool encode_shell_maps(CUtensorMap tm[3][8], void *fbase, long long fstride, const float *ce, const float *ca,
+                       int storage, int nx, int ny, int nz, int pitch, int nr);
 int systolic_reg_rows(int k);
 
 size_t systolic_smem_bytes(int variant);
 // `fmt` is a kernel format code as for the naive scheme; the shared-memory
 // variants (0, 1) take FP32 only.
-cudaError_t systolic_configure(int variant, int fmt);
-int systolic_max_ctas_per_sm(int variant, int fmt);
+// Lossy (absorber) launches need the register kernel (variant >= 2).
+cudaError_t systolic_configure(int variant, int fmt, bool lossy);
+int systolic_max_ctas_per_sm(int variant, int fmt, bool lossy);
 cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant, int fmt);
 cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int fmt);
 

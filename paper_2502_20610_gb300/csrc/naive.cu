@@ -52,12 +52,12 @@ naive_h_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ ey_,
     }
 }
 
-template <class S>
+template <class S, bool LOSSY>
 __global__ void __launch_bounds__(NAIVE_BX *NAIVE_BY)
 naive_e_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ ey_, typename S::T *__restrict__ ez_,
                typename S::T *__restrict__ hx_, typename S::T *__restrict__ hy_, typename S::T *__restrict__ hz_,
-               const float *__restrict__ ce_, int nx, int ny, int nz, int pitch, long long step,
-               const SrcSet src, const Scales sc)
+               const float *__restrict__ ce_, const float *__restrict__ ca_, int nx, int ny, int nz, int pitch,
+               long long step, const SrcSet src, const Scales sc)
 {
     using T = typename S::T;
     const int i = blockIdx.x * NAIVE_BX + threadIdx.x;
@@ -75,11 +75,14 @@ naive_e_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ ey_,
         const float hx = S::dec(__ldg(Hx + p), s3), hy = S::dec(__ldg(Hy + p), s4);
         const float hz = S::dec(__ldg(Hz + p), s5);
         const float ce = __ldg(ce_ + p);
+        const float ca = LOSSY ? __ldg(ca_ + p) : 1.f;
         float ex = S::dec(ex_[p], sc.s[0]), ey = S::dec(ey_[p], sc.s[1]), ez = S::dec(ez_[p], sc.s[2]);
-        // PEC: tangential E on the low planes is never updated
-        if (j > 0 && k > 0) ex = e_x(ex, hz, S::dec(__ldg(Hz + p - pitch), s5), hy, hym, ce);
-        if (i > 0 && k > 0) ey = e_y(ey, hx, hxm, hz, S::dec(__ldg(Hz + p - 1), s5), ce);
-        if (i > 0 && j > 0) ez = e_z(ez, hy, S::dec(__ldg(Hy + p - 1), s4), hx, S::dec(__ldg(Hx + p - pitch), s3), ce);
+        // PEC: tangential E on the low planes is never updated.  Lossy cells:
+        // E <- ca E + cb curl H, with cb in place of dt/eps
+        if (j > 0 && k > 0) ex = e_x(decay<LOSSY>(ca, ex), hz, S::dec(__ldg(Hz + p - pitch), s5), hy, hym, ce);
+        if (i > 0 && k > 0) ey = e_y(decay<LOSSY>(ca, ey), hx, hxm, hz, S::dec(__ldg(Hz + p - 1), s5), ce);
+        if (i > 0 && j > 0)
+            ez = e_z(decay<LOSSY>(ca, ez), hy, S::dec(__ldg(Hy + p - 1), s4), hx, S::dec(__ldg(Hx + p - pitch), s3), ce);
         for (int q = 0; q < src.n; ++q) {
             const SrcDesc &s = src.s[q];
             if (s.idx == p && step < s.n_amp) {
@@ -103,11 +106,11 @@ naive_e_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ ey_,
 // of Fig. 1 in which the update needs no global synchronisation.  The data
 // change inside the launch, so loads are plain (coherent) loads; the block
 // barrier orders each half-step's stores before the next one's loads.
-template <class S>
+template <class S, bool LOSSY>
 __global__ void __launch_bounds__(NAIVE_BLOCK_CELLS)
 naive_block_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ ey_, typename S::T *__restrict__ ez_,
                    typename S::T *__restrict__ hx_, typename S::T *__restrict__ hy_, typename S::T *__restrict__ hz_,
-                   const float *__restrict__ ce_, int nx, int ny, int nz, int pitch, float ndt, long long step0,
+                   const float *__restrict__ ce_, const float *__restrict__ ca_, int nx, int ny, int nz, int pitch, float ndt, long long step0,
                    int nsteps, const SrcSet src, const Scales sc)
 {
     const int q = threadIdx.x;
@@ -117,6 +120,7 @@ naive_block_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ 
     const long long p = i + (long long)pitch * (j + (long long)ny * k);
     const bool ip = i + 1 < nx, jp = j + 1 < ny, kp = k + 1 < nz;
     const float ce = own ? ce_[p] : 0.f;
+    const float ca = LOSSY && own ? ca_[p] : 1.f;
     for (int s = 0; s < nsteps; ++s) {
         if (own) {
             const float exc = S::dec(ex_[p], sc.s[0]), eyc = S::dec(ey_[p], sc.s[1]), ezc = S::dec(ez_[p], sc.s[2]);
@@ -135,11 +139,11 @@ naive_block_kernel(typename S::T *__restrict__ ex_, typename S::T *__restrict__ 
             const float hx = S::dec(hx_[p], sc.s[3]), hy = S::dec(hy_[p], sc.s[4]), hz = S::dec(hz_[p], sc.s[5]);
             float ex = S::dec(ex_[p], sc.s[0]), ey = S::dec(ey_[p], sc.s[1]), ez = S::dec(ez_[p], sc.s[2]);
             if (j > 0 && k > 0)
-                ex = e_x(ex, hz, S::dec(hz_[p - pitch], sc.s[5]), hy, S::dec(hy_[p - sxy], sc.s[4]), ce);
+                ex = e_x(decay<LOSSY>(ca, ex), hz, S::dec(hz_[p - pitch], sc.s[5]), hy, S::dec(hy_[p - sxy], sc.s[4]), ce);
             if (i > 0 && k > 0)
-                ey = e_y(ey, hx, S::dec(hx_[p - sxy], sc.s[3]), hz, S::dec(hz_[p - 1], sc.s[5]), ce);
+                ey = e_y(decay<LOSSY>(ca, ey), hx, S::dec(hx_[p - sxy], sc.s[3]), hz, S::dec(hz_[p - 1], sc.s[5]), ce);
             if (i > 0 && j > 0)
-                ez = e_z(ez, hy, S::dec(hy_[p - 1], sc.s[4]), hx, S::dec(hx_[p - pitch], sc.s[3]), ce);
+                ez = e_z(decay<LOSSY>(ca, ez), hy, S::dec(hy_[p - 1], sc.s[4]), hx, S::dec(hx_[p - pitch], sc.s[3]), ce);
             const long long step = step0 + s;
             for (int qq = 0; qq < src.n; ++qq) {
                 const SrcDesc &d = src.s[qq];
@@ -175,23 +179,36 @@ cudaError_t launch_h(void *const f[6], int nx, int ny, int nz, int pitch, float 
 }
 
 template <class S>
-cudaError_t launch_e(void *const f[6], const float *ce, int nx, int ny, int nz, int pitch, long long step,
-                     const SrcSet &src, const Scales &sc, cudaStream_t st)
+cudaError_t launch_e(void *const f[6], const float *ce, const float *ca, int nx, int ny, int nz, int pitch,
+                     long long step, const SrcSet &src, const Scales &sc, cudaStream_t st)
 {
     using T = typename S::T;
-    naive_e_kernel<S><<<naive_grid(nx, ny, nz), dim3(NAIVE_BX, NAIVE_BY), 0, st>>>(
-        (T *)f[0], (T *)f[1], (T *)f[2], (T *)f[3], (T *)f[4], (T *)f[5], ce, nx, ny, nz, pitch, step, src, sc);
+    if (ca)
+        naive_e_kernel<S, true><<<naive_grid(nx, ny, nz), dim3(NAIVE_BX, NAIVE_BY), 0, st>>>(
+            (T *)f[0], (T *)f[1], (T *)f[2], (T *)f[3], (T *)f[4], (T *)f[5], ce, ca, nx, ny, nz, pitch, step, src,
+            sc);
+    else
+        naive_e_kernel<S, false><<<naive_grid(nx, ny, nz), dim3(NAIVE_BX, NAIVE_BY), 0, st>>>(
+            (T *)f[0], (T *)f[1], (T *)f[2], (T *)f[3], (T *)f[4], (T *)f[5], ce, ca, nx, ny, nz, pitch, step, src,
+            sc);
     return cudaGetLastError();
 }
 
 template <class S>
-cudaError_t launch_block(void *const f[6], const float *ce, int nx, int ny, int nz, int pitch, float neg_dt,
-                         long long step0, int nsteps, const SrcSet &src, const Scales &sc, cudaStream_t st)
+cudaError_t launch_block(void *const f[6], const float *ce, const float *ca, int nx, int ny, int nz, int pitch,
+                         float neg_dt, long long step0, int nsteps, const SrcSet &src, const Scales &sc,
+                         cudaStream_t st)
 {
     using T = typename S::T;
     const int threads = (nx * ny * nz + 31) / 32 * 32;
-    naive_block_kernel<S><<<1, threads, 0, st>>>((T *)f[0], (T *)f[1], (T *)f[2], (T *)f[3], (T *)f[4], (T *)f[5],
-                                                  ce, nx, ny, nz, pitch, neg_dt, step0, nsteps, src, sc);
+    if (ca)
+        naive_block_kernel<S, true><<<1, threads, 0, st>>>((T *)f[0], (T *)f[1], (T *)f[2], (T *)f[3], (T *)f[4],
+                                                            (T *)f[5], ce, ca, nx, ny, nz, pitch, neg_dt, step0,
+                                                            nsteps, src, sc);
+    else
+        naive_block_kernel<S, false><<<1, threads, 0, st>>>((T *)f[0], (T *)f[1], (T *)f[2], (T *)f[3], (T *)f[4],
+                                                             (T *)f[5], ce, ca, nx, ny, nz, pitch, neg_dt, step0,
+                                                             nsteps, src, sc);
     return cudaGetLastError();
 }
 
@@ -199,11 +216,11 @@ cudaError_t launch_block(void *const f[6], const float *ce, int nx, int ny, int 
 
 int naive_block_max_cells() { return NAIVE_BLOCK_CELLS; }
 
-cudaError_t launch_naive_block(void *const f[6], int fmt, const float *ce, int nx, int ny, int nz, int pitch,
-                               float neg_dt, long long step0, int nsteps, const SrcSet &src, const Scales &sc,
-                               cudaStream_t st)
+cudaError_t launch_naive_block(void *const f[6], int fmt, const float *ce, const float *ca, int nx, int ny, int nz,
+                               int pitch, float neg_dt, long long step0, int nsteps, const SrcSet &src,
+                               const Scales &sc, cudaStream_t st)
 {
-    DISPATCH_FORMAT(fmt, S, launch_block<S>(f, ce, nx, ny, nz, pitch, neg_dt, step0, nsteps, src, sc, st));
+    DISPATCH_FORMAT(fmt, S, launch_block<S>(f, ce, ca, nx, ny, nz, pitch, neg_dt, step0, nsteps, src, sc, st));
 }
 
 cudaError_t launch_naive_h(void *const f[6], int fmt, int nx, int ny, int nz, int pitch, float neg_dt,
@@ -212,8 +229,8 @@ cudaError_t launch_naive_h(void *const f[6], int fmt, int nx, int ny, int nz, in
     DISPATCH_FORMAT(fmt, S, launch_h<S>(f, nx, ny, nz, pitch, neg_dt, sc, st));
 }
 
-cudaError_t launch_naive_e(void *const f[6], int fmt, const float *ce, int nx, int ny, int nz, int pitch,
-                           long long step, const SrcSet &src, const Scales &sc, cudaStream_t st)
+cudaError_t launch_naive_e(void *const f[6], int fmt, const float *ce, const float *ca, int nx, int ny, int nz,
+                           int pitch, long long step, const SrcSet &src, const Scales &sc, cudaStream_t st)
 {
-    DISPATCH_FORMAT(fmt, S, launch_e<S>(f, ce, nx, ny, nz, pitch, step, src, sc, st));
+    DISPATCH_FORMAT(fmt, S, launch_e<S>(f, ce, ca, nx, ny, nz, pitch, step, src, sc, st));
 }

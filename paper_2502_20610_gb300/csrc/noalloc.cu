@@ -51,12 +51,12 @@ fdtd_status setup_device(int dev, DeviceState *&out)
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-        e = systolic_configure(NOALLOC_VARIANT, FDTD_STORAGE_F32);
+        e = systolic_configure(NOALLOC_VARIANT, FDTD_STORAGE_F32, false);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-        const int per_sm = systolic_max_ctas_per_sm(NOALLOC_VARIANT, FDTD_STORAGE_F32);
+        const int per_sm = systolic_max_ctas_per_sm(NOALLOC_VARIANT, FDTD_STORAGE_F32, false);
         if (per_sm < 1) return FDTD_ERR_UNSUPPORTED;
         d.scratch = (unsigned char *)p;
         d.max_ctas = sms * per_sm;
@@ -121,6 +121,7 @@ extern "C" fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *
     SysLaunch p;
     for (int k = 0; k < 6; ++k) p.f[k] = d_fields + (size_t)k * n;
     p.ce = d_coef;
+    p.ca = nullptr;
     p.nx = g.nx;
     p.ny = g.ny;
     p.nz = g.nz;

@@ -46,9 +46,10 @@ namespace {
 
 using namespace sysc;
 
-template <int NZ_, class S_>
+template <int NZ_, class S_, bool LOSSY_>
 struct RegTile {
     using S = S_;
+    static constexpr bool LOSSY = LOSSY_;  // conducting cells: E <- ca E + cb curl H
     using T = typename S_::T;
     static constexpr int NZ = NZ_;        // updated z rows (registers 0..NZ-1)
     static constexpr int NR = NZ_ + 1;    // plus the shell row -1
@@ -75,14 +76,15 @@ struct RegTile {
     static_assert((ZBC * 4) % 128 == 0 && (XBC * 4) % 128 == 0, "boxes stay 128-byte aligned");
     static constexpr int FST_B = 6 * (ZB + YB + XB) * EB;  // field staging bytes
     static constexpr int CST_F = ZBC + YBC + XBC;          // coefficient staging floats
+    static constexpr int NCOEF = LOSSY ? 2 : 1;   // FP32 coefficient arrays: cb (dt/eps), ca
     static constexpr unsigned TMA_BYTES =
-        6u * EB * (RY * SW + NR * SW + NR * 16 * XA) + 4u * (RY * SWC + NR * SWC + NR * 16 * XAC);
+        6u * EB * (RY * SW + NR * SW + NR * 16 * XA) + NCOEF * 4u * (RY * SWC + NR * SWC + NR * 16 * XAC);
     static constexpr int CR = 16;                 // coefficient ring rows (>= NR, power of 2)
     static constexpr int CE_F = RY * CR * 32;
     static_assert(CR >= NR, "coefficient ring holds the whole column");
     static constexpr size_t smem_bytes()
     {
-        return FST_B + sizeof(float) * (4 * (size_t)XE_F + XO_F + CE_F + CST_F);
+        return FST_B + sizeof(float) * (4 * (size_t)XE_F + XO_F + NCOEF * (size_t)(CE_F + CST_F));
     }
 };
 
@@ -140,7 +142,10 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     float *const ZSC = reinterpret_cast<float *>(reinterpret_cast<char *>(smem4) + R::FST_B);  // dt/eps shells
     float *const YSC = ZSC + R::ZBC;
     float *const XSC = YSC + R::YBC;
-    float *const XEx = XSC + R::XBC;       // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
+    float *const ZSA = XSC + R::XBC;       // ca shells (lossy only)
+    float *const YSA = ZSA + R::ZBC;
+    float *const XSA = YSA + R::YBC;
+    float *const XEx = (R::LOSSY ? XSA + R::XBC : ZSA);  // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
     float *const XEz = XEx + R::XE_F;
     float *const XHx = XEz + R::XE_F;      // [warp][row i-1][lane]: new H rows r = 0..NZ-1
     float *const XHz = XHx + R::XE_F;
@@ -148,6 +153,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     // dt/eps of each column, indexed by physical z mod CR: a cell's coefficient
     // stays in place while the skewed register rows move past it
     float *const CEs = XO + R::XO_F;       // [warp][physical z mod CR][lane]
+    float *const CAs = CEs + R::CE_F;      // the same for ca (lossy only)
     __shared__ int s_ticket, s_abort;
     __shared__ alignas(8) unsigned long long s_bar;  // staging barrier: one phase per step
     __shared__ unsigned s_seen[3];
@@ -164,6 +170,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #define F4 reinterpret_cast<T *>(P.f[4])
 #define F5 reinterpret_cast<T *>(P.f[5])
 #define CE P.ce
+#define CA P.ca
 #define SC(c) P.sc.s[c]
 #define IS(c) P.sc.is[c]
 #define RND(v, c) S::rnd(v, SC(c), IS(c))
@@ -236,17 +243,19 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
                 const int pz = Az + i - 1 - iv.s + 1;
-                float c = 0.f;
+                float c = 0.f, a = 0.f;
                 if (cin && (unsigned)pz < (unsigned)P.nz) {
                     const long long g = col + sxy * pz;
                     ex[i] = S::dec(S::ld_cg(F0 + g), SC(0)); ey[i] = S::dec(S::ld_cg(F1 + g), SC(1));
                     ez[i] = S::dec(S::ld_cg(F2 + g), SC(2)); hx[i] = S::dec(S::ld_cg(F3 + g), SC(3));
                     hy[i] = S::dec(S::ld_cg(F4 + g), SC(4)); hz[i] = S::dec(S::ld_cg(F5 + g), SC(5));
                     c = __ldg(CE + g);
+                    if (R::LOSSY) a = __ldg(CA + g);
                 } else {
                     ex[i] = ey[i] = ez[i] = hx[i] = hy[i] = hz[i] = 0.f;
                 }
                 CEs[(w * CR + (pz & (CR - 1))) * 32 + lane] = c;
+                if (R::LOSSY) CAs[(w * CR + (pz & (CR - 1))) * 32 + lane] = a;
             }
         }
         if (iv.s > 0 && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.s);
@@ -325,6 +334,11 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 tma_box(ZSC, &P.tm[0][6], x0c, by - 1, bz - 1, &s_bar);
                 tma_box(YSC, &P.tm[1][6], x0c, by - 1, bz - 1, &s_bar);
                 tma_box(XSC, &P.tm[2][6], x0c, by, bz - 1, &s_bar);
+                if (R::LOSSY) {
+                    tma_box(ZSA, &P.tm[0][7], x0c, by - 1, bz - 1, &s_bar);
+                    tma_box(YSA, &P.tm[1][7], x0c, by - 1, bz - 1, &s_bar);
+                    tma_box(XSA, &P.tm[2][7], x0c, by, bz - 1, &s_bar);
+                }
             }
 
             // C. H half-step, top-down in place: H[i] <- H[i-1] - dt curl_f(E[i-1], E[i], ...)
@@ -366,6 +380,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     hy[i] = S::dec(YST[4 * R::YB + i * SW + xl], SC(4));
                     hz[i] = S::dec(YST[5 * R::YB + i * SW + xl], SC(5));
                     CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YSC[i * SWC + xlc];
+                    if (R::LOSSY) CAs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YSA[i * SWC + xlc];
                 }
             } else if (xbox) {  // row -1 takes the lower z shell's H and coefficient
                 const int o = (dy + 1) * SW + (px - x0), oc = (dy + 1) * SWC + (px - x0c);
@@ -373,15 +388,18 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 hy[0] = S::dec(ZST[4 * R::ZB + o], SC(4));
                 hz[0] = S::dec(ZST[5 * R::ZB + o], SC(5));
                 CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZSC[oc];
+                if (R::LOSSY) CAs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZSA[oc];
             } else {  // the lane leaving the tile in x takes the x shell's H and coefficient
                 const T *xs = XST + dy * XA + xe;
                 const float *xsc = XSC + dy * R::XAC + xec;
+                const float *xsa = XSA + dy * R::XAC + xec;
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
                     hx[i] = S::dec(xs[3 * R::XB + i * 16 * XA], SC(3));
                     hy[i] = S::dec(xs[4 * R::XB + i * 16 * XA], SC(4));
                     hz[i] = S::dec(xs[5 * R::XB + i * 16 * XA], SC(5));
                     CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xsc[i * 16 * R::XAC];
+                    if (R::LOSSY) CAs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xsa[i * 16 * R::XAC];
                 }
             }
 #pragma unroll
@@ -417,9 +435,10 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                         const float hx_ym = XHx[(wm * NZ + (i - 1)) * 32 + lane];
                         const float hz_ym = XHz[(wm * NZ + (i - 1)) * 32 + lane];
                         const float c = CEs[(w * CR + ((bz + i - 1) & (CR - 1))) * 32 + lane];
-                        float nex = e_x(ex[i - 1], hz[i], hz_ym, hy[i], hy[i - 1], c);
-                        float ney = e_y(ey[i - 1], hx[i], hx[i - 1], hz[i], hz_xm, c);
-                        float nez = e_z(ez[i - 1], hy[i], hy_xm, hx[i], hx_ym, c);
+                        const float a = R::LOSSY ? CAs[(w * CR + ((bz + i - 1) & (CR - 1))) * 32 + lane] : 1.f;
+                        float nex = e_x(decay<R::LOSSY>(a, ex[i - 1]), hz[i], hz_ym, hy[i], hy[i - 1], c);
+                        float ney = e_y(decay<R::LOSSY>(a, ey[i - 1]), hx[i], hx[i - 1], hz[i], hz_xm, c);
+                        float nez = e_z(decay<R::LOSSY>(a, ez[i - 1]), hy[i], hy_xm, hx[i], hx_ym, c);
                         if (decltype(round)::value) {
                             nex = RND(nex, 0);
                             ney = RND(ney, 1);
@@ -564,19 +583,40 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #undef F4
 #undef F5
 #undef CE
+#undef CA
 #undef SC
 #undef IS
 #undef RND
 #undef STORE6
 
-// 31 x 15 x 12 and 31 x 15 x 8 tiles, each for every kernel format
+// 31 x 15 x 12 and 31 x 15 x 8 tiles, each for every kernel format; the
+// lossy (absorber) form for the 31 x 15 x 12 tile
 template <int NZ>
 struct RegShape {
-    static cudaError_t configure(int fmt) { DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S>>()); }
-    static int per_sm(int fmt) { DISPATCH_FORMAT(fmt, S, occ<RegTile<NZ, S>>()); }
+    static constexpr bool HAS_LOSSY = NZ == 12;
+    static cudaError_t configure(int fmt, bool lossy)
+    {
+        if (lossy) {
+            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S, true>>());
+            return cudaErrorInvalidValue;
+        }
+        DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S, false>>());
+    }
+    static int per_sm(int fmt, bool lossy)
+    {
+        if (lossy) {
+            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, occ<RegTile<NZ, S, true>>());
+            return 0;
+        }
+        DISPATCH_FORMAT(fmt, S, occ<RegTile<NZ, S, false>>());
+    }
     static cudaError_t launch(const SysLaunch &p, int grid, cudaStream_t st, int fmt)
     {
-        DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S>>(p, grid, st));
+        if (p.ca) {
+            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S, true>>(p, grid, st));
+            return cudaErrorInvalidValue;
+        }
+        DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S, false>>(p, grid, st));
     }
     template <class R>
     static cudaError_t set()
@@ -610,9 +650,15 @@ int systolic_reg_rows(int k) { return (k == 0 ? 12 : 8) + 1; }
 
 SysShape systolic_reg_shape(int k) { return SysShape{31, 15, k == 0 ? 12 : 8}; }
 
-cudaError_t systolic_reg_configure(int k, int fmt) { return k == 0 ? RegA::configure(fmt) : RegB::configure(fmt); }
+cudaError_t systolic_reg_configure(int k, int fmt, bool lossy)
+{
+    return k == 0 ? RegA::configure(fmt, lossy) : RegB::configure(fmt, lossy);
+}
 
-int systolic_reg_max_ctas_per_sm(int k, int fmt) { return k == 0 ? RegA::per_sm(fmt) : RegB::per_sm(fmt); }
+int systolic_reg_max_ctas_per_sm(int k, int fmt, bool lossy)
+{
+    return k == 0 ? RegA::per_sm(fmt, lossy) : RegB::per_sm(fmt, lossy);
+}
 
 cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int fmt)
 {

@@ -42,3 +42,9 @@ __device__ __forceinline__ float e_z(float ez, float hy, float hy_im, float hx, 
 
 // Point source: added after the E update with one FP32 rounding.
 __device__ __forceinline__ float add_source(float e, float amp) { return __fadd_rn(e, amp); }
+
+// Conducting cells (the lossy form E <- ca E + cb curl H): the old value is
+// first scaled by ca with one rounding; lossless kernels skip the multiply
+// (ca = 1 would leave E unchanged anyway).
+template <bool LOSSY>
+__device__ __forceinline__ float decay(float ca, float e) { return LOSSY ? __fmul_rn(ca, e) : e; }

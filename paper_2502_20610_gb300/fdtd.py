@@ -113,7 +113,10 @@ TILES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15), "31x15x12": (31, 15, 
 
 
 def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
-                steps_per_launch=0, max_source_steps=0, boundary="pec", tile=None, field_scale=None):
+                steps_per_launch=0, max_source_steps=0, boundary="pec", tile=None, field_scale=None,
+                absorber=None):
+    """absorber: (thickness L, sigma_max, order m) of the graded layer when
+    boundary == "graded"."""
     nz, ny, nx = (int(s) for s in shape_zyx)
     g = Grid(nx, ny, nz)
     c = Coeffs()
@@ -131,6 +134,8 @@ def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
             c.tile[a] = int(t[a])
     b = Boundary()
     b.kind = BOUNDARY[boundary]
+    if absorber is not None:
+        b.thickness, b.sigma_max, b.poly_order = int(absorber[0]), float(absorber[1]), int(absorber[2])
     return g, c, b
 
 
@@ -160,12 +165,16 @@ class Sim:
     scheme: "naive" (one kernel per half-step) or "systolic" (persistent
     skewed-tile kernel).  storage: "f32", "f16" or "bf16" field storage
     (arithmetic is FP32 in every case); field_scale: six powers of two, the
-    16-bit formats store v / s_c.  Fields are exchanged as float32
-    (6, nz, ny, nx) arrays in component order Ex, Ey, Ez, Hx, Hy, Hz.
+    16-bit formats store v / s_c.  boundary: "pec", or "graded" with
+    absorber = (thickness, sigma_max, order): a conducting layer with
+    sigma = sigma_max * sum_a (depth_a / thickness)^order inside the PEC box.
+    Fields are exchanged as float32 (6, nz, ny, nx) arrays in component order
+    Ex, Ey, Ez, Hx, Hy, Hz.
     """
 
     def __init__(self, shape_zyx, eps, dt, scheme="systolic", device=None, timeout_s=2.0,
-                 steps_per_launch=0, max_source_steps=0, tile=None, storage="f32", field_scale=None):
+                 steps_per_launch=0, max_source_steps=0, tile=None, storage="f32", field_scale=None,
+                 boundary="pec", absorber=None):
         import torch
         self._lib = load_library()
         self.shape = tuple(int(s) for s in shape_zyx)
@@ -175,7 +184,8 @@ class Sim:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         g, c, b = make_params(self.shape, dt, scheme=scheme, timeout_s=timeout_s,
                               steps_per_launch=steps_per_launch, max_source_steps=max_source_steps,
-                              tile=tile, storage=storage, field_scale=field_scale)
+                              tile=tile, storage=storage, field_scale=field_scale, boundary=boundary,
+                              absorber=absorber)
         self._params = (g, c, b)
         n = ctypes.c_size_t(0)
         _check(self._lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c), ctypes.byref(b),

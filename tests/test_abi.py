@@ -89,6 +89,24 @@ def test_storage_option_checks(lib):
     assert _ws(lib, g, c, b)[0] == fdtd.FDTD_ERR_INVALID_ARG
 
 
+def test_boundary_option_checks(lib):
+    shape = (40, 40, 40)
+    ok = fdtd.make_params(shape, wl.DT_DEFAULT, boundary="graded", absorber=(8, 0.5, 3))
+    st, n_abs = _ws(lib, *ok)
+    assert st == 0
+    assert n_abs > _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT))[1]  # one more FP32 array
+    assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive", boundary="graded",
+                                      absorber=(8, 0.5, 3), storage="f16"))[0] == 0
+    for bad in ((0, 0.5, 3), (8, -1.0, 3), (8, float("nan"), 3), (8, 0.5, -1), (8, 0.5, 17)):
+        assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, boundary="graded", absorber=bad))[0] == \
+            fdtd.FDTD_ERR_INVALID_ARG, bad
+    # the lossy update is built for the default register tile only
+    for tile in ("31x15x8", "31x15x15", "31x7x15"):
+        assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, boundary="graded", absorber=(8, 0.5, 3),
+                                          tile=tile))[0] == fdtd.FDTD_ERR_UNSUPPORTED
+    assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, boundary="learned"))[0] == fdtd.FDTD_ERR_UNSUPPORTED
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.fdtd_step(None, 1) == fdtd.FDTD_ERR_INVALID_ARG
     assert lib.fdtd_current_step(None) == -1

@@ -1,0 +1,88 @@
+"""Graded-conductivity absorber on the GPU, through the C ABI: both
+schedules bit-identical (FP32 and 16-bit storage), and the FP32 result
+within 1e-4 relative L2 of the FP64 oracle's lossy update."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import bits_equal, rel_l2_per_field
+from paper_2502_20610_gb300 import fdtd
+from paper_2502_20610_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+DT = wl.DT_DEFAULT
+
+
+def run(shape, eps, f0, steps, scheme, absorber, sources=(), storage="f32", scales=None, split=None):
+    sim = fdtd.Sim(shape, eps, DT, scheme=scheme, boundary="graded", absorber=absorber, storage=storage,
+                   field_scale=scales)
+    try:
+        sim.write_fields(torch.as_tensor(np.asarray(f0, dtype=np.float32)).cuda())
+        for (c, i, j, k, J) in sources:
+            sim.add_source(c, i, j, k, J)
+        for n in (split or [steps]):
+            sim.step(n)
+        return sim.read_fields().cpu()
+    finally:
+        sim.close()
+
+
+def oracle(shape, eps, f0, steps, absorber, sources=()):
+    from oracle import YeeOracle
+    from oracle.yee import graded_sigma
+    o = YeeOracle(shape, DT, eps)
+    o.set_eps_sigma(eps, graded_sigma(shape, *absorber), True)
+    o.set_fields(np.asarray(f0, dtype=np.float32).astype(np.float64))
+    for (c, i, j, k, J) in sources:
+        o.add_source(c, i, j, k, J)
+    o.step(steps)
+    return o.fields()
+
+
+@pytest.mark.parametrize("shape,steps,absorber", [
+    ((40, 40, 40), 60, (8, 0.6, 3)),
+    ((47, 35, 66), 45, (6, 1.2, 2)),
+    ((20, 33, 40), 30, (12, 0.3, 3)),   # layers overlap across y and z
+    ((9, 10, 11), 25, (3, 0.8, 1)),     # single-CTA naive path
+])
+def test_absorber_naive_equals_systolic_and_oracle(cuda_device, shape, steps, absorber):
+    eps = wl.si_sio2_eps(shape, 3) if min(shape) >= 20 else wl.random_eps(shape, 3)
+    f0 = wl.random_fields(shape, 3)
+    nz, ny, nx = shape
+    src = [(2, nx // 2, ny // 2, nz // 2, wl.gaussian_pulse_source(steps, DT)),
+           (0, 1, ny // 3, nz // 3, wl.sine_source(steps, DT))]  # inside the layer
+    a = run(shape, eps, f0, steps, "naive", absorber, src)
+    b = run(shape, eps, f0, steps, "systolic", absorber, src, split=[steps // 2, steps - steps // 2])
+    assert bits_equal(a, b)
+    err = rel_l2_per_field(b.numpy(), oracle(shape, eps, f0, steps, absorber, src))
+    assert max(err.values()) < 1e-4, err
+
+
+@pytest.mark.parametrize("storage,scales", [("f16", None), ("bf16", (1, 2, 0.5, 1, 1, 0.25))])
+def test_absorber_16bit_naive_equals_systolic(cuda_device, storage, scales):
+    shape = (36, 30, 50)
+    eps = wl.si_sio2_eps(shape, 4)
+    f0 = wl.random_fields(shape, 4)
+    src = [(2, 25, 15, 18, wl.gaussian_pulse_source(50, DT))]
+    a = run(shape, eps, f0, 50, "naive", (8, 0.6, 3), src, storage, scales)
+    b = run(shape, eps, f0, 50, "systolic", (8, 0.6, 3), src, storage, scales)
+    assert bits_equal(a, b)
+
+
+def test_absorber_takes_the_energy(cuda_device):
+    # a dipole pulse radiated into a box lined with 12 absorbing cells: after
+    # the source is off the field energy falls below 5% (PEC alone keeps it)
+    shape = (48, 48, 48)
+    eps = np.ones(shape)
+    J = wl.gaussian_pulse_source(270, DT, wavelength=10.0)
+    left = []
+    for smax in (0.0, 0.6):
+        sim = fdtd.Sim(shape, eps, DT, boundary="graded", absorber=(12, smax, 3))
+        sim.add_source(2, 24, 24, 24, J)
+        sim.step(270)
+        e1 = float((sim.read_fields().double() ** 2).sum())
+        sim.step(300)
+        e2 = float((sim.read_fields().double() ** 2).sum())
+        sim.close()
+        left.append(e2 / e1)
+    assert left[0] > 0.5 and left[1] < 0.05, left
