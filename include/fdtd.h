@@ -82,12 +82,32 @@ typedef struct {
     int32_t steps_per_launch; /* systolic: steps per persistent launch; <= 0 = 1024 */
 } fdtd_coeffs;
 
+/* Boundary inside the PEC box.
+ *   FDTD_BOUNDARY_PEC: none.
+ *   FDTD_BOUNDARY_GRADED_ABSORBER: a conducting layer (the lossy structure
+ *     field of Sec. 4) of `thickness` cells at every wall,
+ *     sigma = sigma_max * sum_a (depth_a / thickness)^poly_order with depth_a
+ *     = thickness - i inside the low layer, i - (N-1-thickness) inside the
+ *     high one; the E update becomes E <- ca E + cb (curl H - J) with
+ *     ca = (1 - g)/(1 + g), cb = (dt/eps)/(1 + g), g = sigma dt/(2 eps),
+ *     formed in FP64 and rounded to FP32 per cell.  Systolic scheme: the
+ *     default 31x15x12 tile only.
+ *   FDTD_BOUNDARY_LEARNED: every cell takes the Yee step of the PEC box,
+ *     then the cells within `thickness` of a wall add the correction of the
+ *     network `model` (host, fdtd_mlp_param_count() floats, copied; layout
+ *     at fdtd_mlp_*) computed from the 3x3x3 stencils of the state at steps
+ *     n and n-1 (the state before the first step, and after
+ *     fdtd_write_fields, has S^{-1} = 0) to the values the PEC walls get
+ *     wrong: tangential E on a cell of a low face, tangential H on a cell of
+ *     a high face.  A zero network is the PEC box.
+ *     Naive scheme and FP32 storage only (the update needs the whole previous
+ *     level every step, which the systolic tiles do not keep). */
 typedef struct {
-    int32_t kind;       /* FDTD_BOUNDARY_*; this build: PEC only */
-    int32_t thickness;  /* absorber / learned layer thickness in cells */
-    double sigma_max;   /* graded absorber peak conductivity */
-    int32_t poly_order; /* graded absorber grading order */
-    const void *model;  /* learned boundary parameters (host) */
+    int32_t kind;       /* FDTD_BOUNDARY_* */
+    int32_t thickness;  /* absorber / learned layer thickness in cells, >= 1 */
+    double sigma_max;   /* graded absorber peak conductivity, >= 0 */
+    int32_t poly_order; /* graded absorber grading order, 0..16 */
+    const void *model;  /* learned boundary parameters (host floats) */
 } fdtd_boundary;
 
 typedef struct fdtd_sim *fdtd_handle;
@@ -211,6 +231,50 @@ fdtd_status fdtd_debug_set(fdtd_handle h, int32_t kind, int64_t ticket, int64_t 
  * FDTD_ERR_TIMEOUT if a device wait ran out, FDTD_ERR_CUDA on a CUDA error,
  * FDTD_ERR_INVALID_ARG for null pointers, n_steps < 0 or dt <= 0. */
 #define FDTD_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+
+/* Learned boundary network (the benchmark spec's learned absorbing boundary; the
+ * paper has no counterpart): f(x) = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3,
+ * 324 -> 64 -> 64 -> 6, FP32.  Parameter vector, in this order: W1 [64][324],
+ * b1 [64], W2 [64][64], b2 [64], W3 [6][64], b3 [6] (row = output unit).
+ * Input x: x[(s*6 + c)*27 + (dz+1)*9 + (dy+1)*3 + (dx+1)] for the fields c =
+ * Ex..Hz at step n (s = 0) and n-1 (s = 1) around the cell, 0 outside the
+ * domain.  A layer cell takes S^{n+1} = Yee(S^n) + r f(x / r), Yee = the PEC
+ * box's own step, r = sqrt(mean x^2) (r < 1e-30 counts as a zero stencil:
+ * no correction).  Training pairs (x_hat, y_hat) = (x / r, (S^{n+1}_ref -
+ * Yee(S^n))(centre) / r), zeros when r < 1e-30; loss
+ * = mean over samples and outputs of (f(x_hat) - y_hat)^2.  All pointers
+ * named d_* are device memory; calls are asynchronous on `stream` unless
+ * they return a host value.  Errors: INVALID_ARG, OOM (scratch too small),
+ * CUDA. */
+int64_t fdtd_mlp_param_count(void);
+/* Scratch for minibatches of `batch` samples out of n_samples. */
+fdtd_status fdtd_mlp_scratch_size(int32_t batch, int64_t n_samples, size_t *bytes);
+/* d_y [n][6] = f(d_x [n][324]), in minibatches of `batch`. */
+fdtd_status fdtd_mlp_forward(const float *d_params, const float *d_x, int64_t n, float *d_y, int32_t batch,
+                             void *d_scratch, size_t scratch_bytes, void *stream);
+/* Gradient of the loss of n samples (scratch for batch = n) into d_grad;
+ * *loss (host, may be NULL) receives the loss.  Synchronous. */
+fdtd_status fdtd_mlp_grad(const float *d_params, const float *d_x, const float *d_y, int32_t n, float *d_grad,
+                          double *loss, void *d_scratch, size_t scratch_bytes, void *stream);
+/* Adam (lr, beta 0.9 / 0.999, eps 1e-8) over `epochs` passes of shuffled
+ * whole minibatches of n samples; d_params is updated in place; *last_epoch_loss
+ * (host, may be NULL) receives the mean loss of the last epoch.  Synchronous. */
+fdtd_status fdtd_mlp_train(float *d_params, const float *d_x, const float *d_y, int64_t n, int32_t batch,
+                           int32_t epochs, double lr, uint64_t seed, void *d_scratch, size_t scratch_bytes,
+                           void *stream, double *last_epoch_loss);
+/* Training pairs from a reference simulation `h` (FP32 storage, no learned
+ * boundary), typically one with a thick graded absorber: the box [lo, hi)
+ * (cells, x y z) is the domain the learned boundary will see.  The call
+ * steps h by n_steps + 1 and after each of the last n_steps records
+ * per_step pairs for cells drawn uniformly (seeded) from the cells within
+ * `thickness` of the box's faces, with stencil cells outside the box read
+ * as 0 and Yee(S^n) the box's own PEC step of the cell (h's coefficients);
+ * pair s*per_step + q goes to d_x [..][324], d_y [..][6].  Scratch:
+ * fdtd_learned_record_scratch_size.  Synchronous. */
+fdtd_status fdtd_learned_record_scratch_size(fdtd_handle h, int32_t per_step, size_t *bytes);
+fdtd_status fdtd_learned_record(fdtd_handle h, const int32_t lo[3], const int32_t hi[3], int32_t thickness,
+                                int32_t n_steps, int32_t per_step, uint64_t seed, float *d_x, float *d_y,
+                                void *d_scratch, size_t scratch_bytes);
 fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *d_fields, const float *d_coef,
                                        double dt, int64_t n_steps, void *stream);
 

@@ -14,18 +14,22 @@ Input layout: x[(s*6 + c)*27 + (dz+1)*9 + (dy+1)*3 + (dx+1)], s = 0 for the
 fields at step n, 1 for step n-1, c = Ex..Hz, stencil offsets in -1..1;
 cells outside the domain read 0.
 Scale equivariance: r = sqrt(mean(x^2)); the network sees x / r and predicts
-the change of the centre cell's six values in units of r:
-    S^{n+1}(centre) = S^n(centre) + r * f(x / r)      (r = 0: unchanged).
+a correction of the centre cell's six values, in units of r, to the Yee
+step of the domain on its own (PEC walls), Yee_D:
+    S^{n+1}(centre) = Yee_D(S^n)(centre) + r * f(x / r)   (r < 1e-30: + 0).
 Loss of a batch: mean over samples and the 6 outputs of (f(x_hat) - y_hat)^2,
-with y_hat = (S^{n+1} - S^n)(centre) / r.
+with y_hat = (S^{n+1}_ref - Yee_D(S^n))(centre) / r.
 
 Learned-boundary step (the layer = cells within `thickness` of a wall):
-    every cell takes the Yee step, then every layer cell is overwritten with
-    the network's prediction from the stencils of S^n and S^{n-1}.
+    every cell takes the Yee step, then every layer cell adds the network's
+    correction from the stencils of S^n and S^{n-1} to the components its
+    walls get wrong: tangential E on a low face, tangential H on a high face
+    (every other value of the Yee step is already the reference's).
 """
 import numpy as np
 
 N_IN, N_H, N_OUT = 324, 64, 6
+R_MIN = 1e-30  # a smaller stencil RMS counts as a zero stencil
 SIZES = [("W1", (N_H, N_IN)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)),
          ("W3", (N_OUT, N_H)), ("b3", (N_OUT,))]
 N_PARAMS = sum(int(np.prod(s)) for _, s in SIZES)
@@ -109,14 +113,28 @@ def stencil_inputs(cur, prev, cells):
     return out
 
 
-def predict_update(theta, x):
-    """S^{n+1}(centre) for stencil inputs x [B, 324] (scale-equivariant form)."""
+def correction(theta, x):
+    """r f(x / r) for stencil inputs x [B, 324] (0 where r < R_MIN)."""
     x = np.asarray(x, dtype=np.float64)
-    centre = x[:, [c * 27 + 13 for c in range(6)]]
     r = np.sqrt(np.mean(x ** 2, axis=1))
-    safe = np.where(r > 0, r, 1.0)
+    live = r >= R_MIN
+    safe = np.where(live, r, 1.0)
     f, _ = forward(theta, x / safe[:, None])
-    return np.where((r > 0)[:, None], centre + r[:, None] * f, centre)
+    return np.where(live[:, None], r[:, None] * f, 0.0)
+
+
+def tangent_mask(cells, shape_zyx):
+    """[B, 6] booleans: tangential E on the low faces, tangential H on the
+    high faces that each cell (x, y, z) lies on."""
+    nz, ny, nx = shape_zyx
+    c = np.asarray(cells)
+    x, y, z = c[:, 0], c[:, 1], c[:, 2]
+    m = np.zeros((len(c), 6), bool)
+    for lo, comps in ((x == 0, (1, 2)), (y == 0, (0, 2)), (z == 0, (0, 1)),
+                      (x == nx - 1, (4, 5)), (y == ny - 1, (3, 5)), (z == nz - 1, (3, 4))):
+        for k in comps:
+            m[:, k] |= lo
+    return m
 
 
 def layer_cells(shape_zyx, thickness):
@@ -132,21 +150,22 @@ def layer_cells(shape_zyx, thickness):
 def learned_run(shape, eps, fields0, steps, theta, thickness=4, sources=(), dt=None, quantize=True,
                 prev0=None):
     """FP64 learned-boundary run: the Yee oracle steps every cell, then the
-    layer cells take the network's prediction.  Returns (S^n, S^{n-1})."""
+    layer cells add the network's correction.  Returns (S^n, S^{n-1})."""
     from .yee import YeeOracle
     o = YeeOracle(shape, dt, eps, quantize_ce_f32=quantize)
     o.set_fields(fields0)
     for (c, i, j, k, J) in sources:
         o.add_source(c, i, j, k, J)
     cells = layer_cells(shape, thickness)
+    mask = tangent_mask(cells, shape)
     prev = np.zeros((6,) + tuple(shape)) if prev0 is None else np.asarray(prev0, dtype=np.float64)
     cur = o.fields()
     for _ in range(steps):
         x = stencil_inputs(cur, prev, cells)
-        pred = predict_update(theta, x)
+        corr = np.where(mask, correction(theta, x), 0.0)
         o.step(1)
         nxt = o.fields()
-        nxt[:, cells[:, 2], cells[:, 1], cells[:, 0]] = pred.T
+        nxt[:, cells[:, 2], cells[:, 1], cells[:, 0]] += corr.T
         o.set_fields(nxt)
         prev, cur = cur, nxt
     return cur, prev

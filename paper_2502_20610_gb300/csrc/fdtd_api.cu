@@ -3,6 +3,7 @@
 // The C ABI is declared (and documented) in include/fdtd.h.
 #include "fdtd.h"
 #include "internal.h"
+#include "mlp.h"
 
 #include <cudaTypedefs.h>
 
@@ -11,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <random>
 #include <vector>
 
 namespace {
@@ -24,6 +26,10 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     size_t fields[6], ce, ca, stage, src, progress, tiles, ctrl, total;
+    // learned boundary: network, previous state, layer and band cell lists,
+    // layer predictions
+    size_t params, prev, layer, band, pred;
+    long long nlayer, nband;
     int eb;     // bytes per stored field value (4 FP32, 2 FP16/BF16)
     int pitch;  // elements per x row in device memory (nx rounded up to 16 bytes)
     int variant, tx, ty, tz;  // systolic tile shape
@@ -33,6 +39,31 @@ struct Layout {
 };
 
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Cells within distance t of a wall (min over axes of the distance to the
+// nearest face < t): the total minus the inner box.
+long long cells_within(const fdtd_grid &g, int t)
+{
+    const long long ix = std::max(0, g.nx - 2 * t), iy = std::max(0, g.ny - 2 * t), iz = std::max(0, g.nz - 2 * t);
+    return (long long)g.nx * g.ny * g.nz - ix * iy * iz;
+}
+
+// (x, y, z) of those cells, x fastest.
+void list_cells_within(const fdtd_grid &g, int t, std::vector<int> &out)
+{
+    out.clear();
+    for (int k = 0; k < g.nz; ++k)
+        for (int j = 0; j < g.ny; ++j)
+            for (int i = 0; i < g.nx; ++i) {
+                const int d = std::min(std::min(std::min(i, g.nx - 1 - i), std::min(j, g.ny - 1 - j)),
+                                       std::min(k, g.nz - 1 - k));
+                if (d < t) {
+                    out.push_back(i);
+                    out.push_back(j);
+                    out.push_back(k);
+                }
+            }
+}
 
 constexpr int DEFAULT_VARIANT = 2;  // register-resident 31 x 15 x 12 with TMA shells: fastest measured
 
@@ -68,6 +99,22 @@ bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, const fdtd_boundary &
     off = align_up(off + sizeof(float) * (size_t)n);
     L.ca = off;  // E decay of conducting cells (absorber)
     if (b.kind == FDTD_BOUNDARY_GRADED_ABSORBER) off = align_up(off + sizeof(float) * (size_t)n);
+    L.nlayer = L.nband = 0;
+    L.params = L.prev = L.layer = L.band = L.pred = off;
+    if (b.kind == FDTD_BOUNDARY_LEARNED) {
+        L.nlayer = cells_within(g, b.thickness);
+        L.nband = cells_within(g, b.thickness + 1);
+        L.params = off;
+        off = align_up(off + sizeof(float) * (size_t)mlpnet::NPARAM);
+        L.prev = off;
+        off = align_up(off + 6 * align_up(sizeof(float) * (size_t)n));
+        L.layer = off;
+        off = align_up(off + 3 * sizeof(int) * (size_t)L.nlayer);
+        L.band = off;
+        off = align_up(off + 3 * sizeof(int) * (size_t)L.nband);
+        L.pred = off;
+        off = align_up(off + 6 * sizeof(float) * (size_t)L.nlayer);
+    }
     L.stage = off;
     if (c.storage != FDTD_STORAGE_F32) off = align_up(off + sizeof(float) * (size_t)g.nx * g.ny * g.nz);
     L.source_steps = c.max_source_steps > 0 ? c.max_source_steps : DEFAULT_SOURCE_STEPS;
@@ -134,7 +181,12 @@ fdtd_status check_args(const fdtd_grid *g, const fdtd_coeffs *c, const fdtd_boun
         // the register kernel's 31 x 15 x 12 tile is the one built with the lossy update
         if (c->scheme == FDTD_SCHEME_SYSTOLIC && pick_variant(*c) != 2) return FDTD_ERR_UNSUPPORTED;
     }
-    if (b->kind == FDTD_BOUNDARY_LEARNED) return FDTD_ERR_UNSUPPORTED;
+    if (b->kind == FDTD_BOUNDARY_LEARNED) {
+        if (b->thickness < 1 || !b->model) return FDTD_ERR_INVALID_ARG;
+        // the layer update needs the whole previous level every step: the
+        // naive scheme, FP32 fields
+        if (c->scheme != FDTD_SCHEME_NAIVE || c->storage != FDTD_STORAGE_F32) return FDTD_ERR_UNSUPPORTED;
+    }
     return FDTD_OK;
 }
 
@@ -292,6 +344,9 @@ struct fdtd_sim {
     void *f[6];
     float *ce;
     float *ca;     // E decay per cell (absorber), else null
+    float *params, *prev, *pred;  // learned boundary (else null)
+    int *layer, *band;
+    int layer_grid;
     float *stage;  // dense FP32 component (16-bit storage), else null
     Scales sc;
     int fmt;       // kernel format (storage.cuh): the storage, or its uniform-scale variant
@@ -404,6 +459,13 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     for (int k = 0; k < 6; ++k) h->f[k] = h->ws + L.fields[k];
     h->ce = (float *)(h->ws + L.ce);
     h->ca = boundary->kind == FDTD_BOUNDARY_GRADED_ABSORBER ? (float *)(h->ws + L.ca) : nullptr;
+    const bool learned = boundary->kind == FDTD_BOUNDARY_LEARNED;
+    h->params = learned ? (float *)(h->ws + L.params) : nullptr;
+    h->prev = learned ? (float *)(h->ws + L.prev) : nullptr;
+    h->pred = learned ? (float *)(h->ws + L.pred) : nullptr;
+    h->layer = learned ? (int *)(h->ws + L.layer) : nullptr;
+    h->band = learned ? (int *)(h->ws + L.band) : nullptr;
+    h->layer_grid = 0;
     h->stage = coeffs->storage != FDTD_STORAGE_F32 ? (float *)(h->ws + L.stage) : nullptr;
     for (int k = 0; k < 6; ++k) {
         const float sk = coeffs->storage != FDTD_STORAGE_F32 && coeffs->field_scale[k] != 0.f ? coeffs->field_scale[k]
@@ -467,6 +529,22 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     for (int k = 0; k < 6 && e == cudaSuccess; ++k)  // all-zero bits are +0 in every format
         e = cudaMemsetAsync(h->f[k], 0, (size_t)L.eb * padded, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ctrl, 0, 64 * sizeof(int), h->stream);
+    std::vector<int> lcells, bcells;
+    if (e == cudaSuccess && learned) {
+        list_cells_within(*grid, boundary->thickness, lcells);
+        list_cells_within(*grid, boundary->thickness + 1, bcells);
+        e = cudaMemcpyAsync(h->params, boundary->model, sizeof(float) * mlpnet::NPARAM, cudaMemcpyDefault, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->prev, 0, L.layer - L.prev, h->stream);
+        if (e == cudaSuccess && !lcells.empty())
+            e = cudaMemcpyAsync(h->layer, lcells.data(), sizeof(int) * lcells.size(), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess && !bcells.empty())
+            e = cudaMemcpyAsync(h->band, bcells.data(), sizeof(int) * bcells.size(), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = learned_layer_configure();
+        int dev = 0, sms = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        h->layer_grid = sms;
+    }
     if (e == cudaSuccess && L.ntiles_max > 0)
         e = cudaMemsetAsync(h->progress, 0, sizeof(unsigned) * (size_t)L.ntiles_max, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -548,6 +626,7 @@ fdtd_status fdtd_write_fields(fdtd_handle h, const float *src)
         }
     }
     CK(cudaMemsetAsync(h->ctrl + 1, 0, 3 * sizeof(int), h->stream));
+    if (h->prev) CK(cudaMemsetAsync(h->prev, 0, h->L.layer - h->L.prev, h->stream));  // S^{n-1} := 0
     h->failed = false;
     return FDTD_OK;
 }
@@ -559,6 +638,24 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
     if (h->c.scheme == FDTD_SCHEME_NAIVE) {
         const float ndt = -(float)h->c.dt;
         const long long cells = (long long)h->g.nx * h->g.ny * h->g.nz;
+        if (h->params) {  // learned boundary: Yee everywhere, then the network's correction on the wall layer
+            float *f0 = (float *)h->f[0];
+            const long long fs = (long long)(h->L.fields[1] - h->L.fields[0]) / 4;
+            const long long ps = (long long)align_up(sizeof(float) * (size_t)h->L.pitch * h->g.ny * h->g.nz) / 4;
+            if (fs != ps) return FDTD_ERR_STATE;  // previous-state arrays mirror the field layout
+            for (int64_t s = 0; s < n; ++s) {
+                CK(learned_layer_predict(h->params, f0, h->prev, fs, h->L.pitch, h->g.nx, h->g.ny, h->g.nz,
+                                         h->layer, (int)h->L.nlayer, h->pred, h->layer_grid, h->stream));
+                CK(learned_copy_cells(h->prev, f0, fs, h->L.pitch, h->g.ny, h->band, (int)h->L.nband, h->stream));
+                CK(launch_naive_h(h->f, h->fmt, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->sc, h->stream));
+                CK(launch_naive_e(h->f, h->fmt, h->ce, h->ca, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->step, h->src,
+                                  h->sc, h->stream));
+                CK(learned_layer_scatter(f0, fs, h->L.pitch, h->g.ny, h->layer, (int)h->L.nlayer, h->pred, h->stream));
+                h->launches += 5;
+                h->step += 1;
+            }
+            return FDTD_OK;
+        }
         if (cells <= naive_block_max_cells()) {  // one CTA holds the domain: no global sync
             while (n > 0) {
                 const int T = (int)std::min<int64_t>(n, 1 << 20);
@@ -689,6 +786,114 @@ const char *fdtd_status_string(fdtd_status s)
 }
 
 void fdtd_destroy(fdtd_handle h) { delete h; }
+
+// ------------------------------------------------ learned-boundary network
+
+int64_t fdtd_mlp_param_count(void) { return mlpnet::NPARAM; }
+
+fdtd_status fdtd_mlp_scratch_size(int32_t batch, int64_t n_samples, size_t *bytes)
+{
+    if (!bytes || batch < 1 || n_samples < 0) return FDTD_ERR_INVALID_ARG;
+    *bytes = mlp_scratch_bytes(batch, n_samples);
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_mlp_forward(const float *d_params, const float *d_x, int64_t n, float *d_y, int32_t batch,
+                             void *d_scratch, size_t scratch_bytes, void *stream)
+{
+    if (!d_params || (n > 0 && (!d_x || !d_y)) || n < 0 || batch < 1 || !d_scratch) return FDTD_ERR_INVALID_ARG;
+    if (scratch_bytes < mlp_scratch_bytes(batch, 0)) return FDTD_ERR_OOM;
+    CK(mlp_forward(d_params, d_x, n, d_y, d_scratch, batch, (cudaStream_t)stream));
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_mlp_grad(const float *d_params, const float *d_x, const float *d_y, int32_t n, float *d_grad,
+                          double *loss, void *d_scratch, size_t scratch_bytes, void *stream)
+{
+    if (!d_params || !d_x || !d_y || !d_grad || n < 1 || !d_scratch) return FDTD_ERR_INVALID_ARG;
+    if (scratch_bytes < mlp_scratch_bytes(n, 0)) return FDTD_ERR_OOM;
+    CK(mlp_grad(d_params, d_x, d_y, n, d_grad, loss, d_scratch, n, (cudaStream_t)stream));
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_mlp_train(float *d_params, const float *d_x, const float *d_y, int64_t n, int32_t batch,
+                           int32_t epochs, double lr, uint64_t seed, void *d_scratch, size_t scratch_bytes,
+                           void *stream, double *last_epoch_loss)
+{
+    if (!d_params || !d_x || !d_y || n < 1 || batch < 1 || batch > n || epochs < 0 || !(lr > 0.0) || !d_scratch ||
+        n > (1ll << 31) - 1)
+        return FDTD_ERR_INVALID_ARG;
+    if (scratch_bytes < mlp_scratch_bytes(batch, n)) return FDTD_ERR_OOM;
+    CK(mlp_train(d_params, d_x, d_y, n, batch, epochs, lr, seed, d_scratch, (cudaStream_t)stream,
+                 last_epoch_loss));
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_learned_record_scratch_size(fdtd_handle h, int32_t per_step, size_t *bytes)
+{
+    if (!h || !bytes || per_step < 1) return FDTD_ERR_INVALID_ARG;
+    const size_t arr = align_up(sizeof(float) * (size_t)h->L.pitch * h->g.ny * h->g.nz);
+    *bytes = 12 * arr + align_up(3 * sizeof(int) * (size_t)per_step);
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_learned_record(fdtd_handle h, const int32_t lo[3], const int32_t hi[3], int32_t thickness,
+                                int32_t n_steps, int32_t per_step, uint64_t seed, float *d_x, float *d_y,
+                                void *d_scratch, size_t scratch_bytes)
+{
+    if (!h || !lo || !hi || thickness < 1 || n_steps < 0 || per_step < 1 || !d_x || !d_y || !d_scratch)
+        return FDTD_ERR_INVALID_ARG;
+    if (h->c.storage != FDTD_STORAGE_F32 || h->params) return FDTD_ERR_UNSUPPORTED;
+    const int n3[3] = {h->g.nx, h->g.ny, h->g.nz};
+    for (int a = 0; a < 3; ++a)
+        if (lo[a] < 0 || hi[a] > n3[a] || hi[a] - lo[a] < 1) return FDTD_ERR_INVALID_ARG;
+    size_t need = 0;
+    fdtd_learned_record_scratch_size(h, per_step, &need);
+    if (scratch_bytes < need) return FDTD_ERR_OOM;
+    const size_t arr = align_up(sizeof(float) * (size_t)h->L.pitch * h->g.ny * h->g.nz);
+    const long long fs = (long long)(h->L.fields[1] - h->L.fields[0]) / 4;
+    if ((long long)(arr / 4) != fs) return FDTD_ERR_STATE;
+    char *base = (char *)d_scratch;
+    float *prev = (float *)base, *cur = (float *)(base + 6 * arr);
+    int *cells = (int *)(base + 12 * arr);
+    float *f0 = (float *)h->f[0];
+    const int ilo[3] = {lo[0], lo[1], lo[2]}, ihi[3] = {hi[0], hi[1], hi[2]};
+    // layer region of the box: cells within `thickness` of one of its faces
+    std::mt19937_64 rng(seed);
+    auto in_layer = [&](int x, int y, int z) {
+        const int d = std::min(std::min(std::min(x - lo[0], hi[0] - 1 - x), std::min(y - lo[1], hi[1] - 1 - y)),
+                               std::min(z - lo[2], hi[2] - 1 - z));
+        return d < thickness;
+    };
+    std::vector<int> pick(3 * (size_t)per_step);
+    CK(cudaMemcpyAsync(prev, f0, 6 * arr, cudaMemcpyDeviceToDevice, h->stream));
+    fdtd_status st = fdtd_step(h, 1);
+    if (st != FDTD_OK) return st;
+    CK(cudaMemcpyAsync(cur, f0, 6 * arr, cudaMemcpyDeviceToDevice, h->stream));
+    for (int s = 0; s < n_steps; ++s) {
+        st = fdtd_step(h, 1);
+        if (st != FDTD_OK) return st;
+        for (int q = 0; q < per_step; ++q) {
+            int x, y, z;
+            do {
+                x = lo[0] + (int)(rng() % (unsigned long long)(hi[0] - lo[0]));
+                y = lo[1] + (int)(rng() % (unsigned long long)(hi[1] - lo[1]));
+                z = lo[2] + (int)(rng() % (unsigned long long)(hi[2] - lo[2]));
+            } while (!in_layer(x, y, z));
+            pick[3 * q] = x;
+            pick[3 * q + 1] = y;
+            pick[3 * q + 2] = z;
+        }
+        CK(cudaMemcpyAsync(cells, pick.data(), sizeof(int) * pick.size(), cudaMemcpyHostToDevice, h->stream));
+        CK(mlp_record(prev, cur, f0, fs, h->L.pitch, h->g.ny, ilo, ihi, cells, per_step, h->ce, h->ca,
+                      -(float)h->c.dt, d_x + (size_t)s * per_step * mlpnet::NI,
+                      d_y + (size_t)s * per_step * mlpnet::NO, h->stream));
+        CK(cudaMemcpyAsync(prev, cur, 6 * arr, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(cur, f0, 6 * arr, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));  // the host cell list is reused next step
+    }
+    return fdtd_sync(h);
+}
 
 fdtd_status fdtd_debug_set(fdtd_handle h, int32_t kind, int64_t ticket, int64_t param, int64_t param2)
 {

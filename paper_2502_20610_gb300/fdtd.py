@@ -24,7 +24,9 @@ DEBUG_NONE, DEBUG_SKIP_PUBLISH, DEBUG_DELAY, DEBUG_ORDER = range(4)
 EXPORTS = ("fdtd_workspace_size", "fdtd_create", "fdtd_add_source", "fdtd_write_fields",
            "fdtd_step", "fdtd_read_fields", "fdtd_sync", "fdtd_current_step",
            "fdtd_set_current_step", "fdtd_launch_count", "fdtd_status_string", "fdtd_destroy",
-           "fdtd_debug_set", "fdtd_systolic_step_noalloc")
+           "fdtd_debug_set", "fdtd_systolic_step_noalloc", "fdtd_mlp_param_count", "fdtd_mlp_scratch_size",
+           "fdtd_mlp_forward", "fdtd_mlp_grad", "fdtd_mlp_train", "fdtd_learned_record_scratch_size",
+           "fdtd_learned_record")
 
 
 class Grid(ctypes.Structure):
@@ -91,6 +93,23 @@ def load_library(path=LIB_PATH):
     lib.fdtd_debug_set.argtypes = [P, I32, I64, I64, I64]
     lib.fdtd_systolic_step_noalloc.restype = st
     lib.fdtd_systolic_step_noalloc.argtypes = [P, P, P, ctypes.c_double, I64, P]
+    SZ = ctypes.c_size_t
+    lib.fdtd_mlp_param_count.restype = I64
+    lib.fdtd_mlp_param_count.argtypes = []
+    lib.fdtd_mlp_scratch_size.restype = st
+    lib.fdtd_mlp_scratch_size.argtypes = [I32, I64, ctypes.POINTER(SZ)]
+    lib.fdtd_mlp_forward.restype = st
+    lib.fdtd_mlp_forward.argtypes = [P, P, I64, P, I32, P, SZ, P]
+    lib.fdtd_mlp_grad.restype = st
+    lib.fdtd_mlp_grad.argtypes = [P, P, P, I32, P, ctypes.POINTER(ctypes.c_double), P, SZ, P]
+    lib.fdtd_mlp_train.restype = st
+    lib.fdtd_mlp_train.argtypes = [P, P, P, I64, I32, I32, ctypes.c_double, ctypes.c_uint64, P, SZ, P,
+                                   ctypes.POINTER(ctypes.c_double)]
+    lib.fdtd_learned_record_scratch_size.restype = st
+    lib.fdtd_learned_record_scratch_size.argtypes = [P, I32, ctypes.POINTER(SZ)]
+    lib.fdtd_learned_record.restype = st
+    lib.fdtd_learned_record.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I32), I32, I32, I32, ctypes.c_uint64,
+                                        P, P, P, SZ]
     _lib = lib
     return lib
 
@@ -114,9 +133,10 @@ TILES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15), "31x15x12": (31, 15, 
 
 def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
                 steps_per_launch=0, max_source_steps=0, boundary="pec", tile=None, field_scale=None,
-                absorber=None):
+                absorber=None, learned=None):
     """absorber: (thickness L, sigma_max, order m) of the graded layer when
-    boundary == "graded"."""
+    boundary == "graded"; learned: (thickness, params) when boundary ==
+    "learned" (params: float32 numpy array, kept alive by the caller)."""
     nz, ny, nx = (int(s) for s in shape_zyx)
     g = Grid(nx, ny, nz)
     c = Coeffs()
@@ -136,6 +156,9 @@ def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
     b.kind = BOUNDARY[boundary]
     if absorber is not None:
         b.thickness, b.sigma_max, b.poly_order = int(absorber[0]), float(absorber[1]), int(absorber[2])
+    if learned is not None:
+        b.thickness = int(learned[0])
+        b.model = learned[1].ctypes.data
     return g, c, b
 
 
@@ -167,14 +190,16 @@ class Sim:
     (arithmetic is FP32 in every case); field_scale: six powers of two, the
     16-bit formats store v / s_c.  boundary: "pec", or "graded" with
     absorber = (thickness, sigma_max, order): a conducting layer with
-    sigma = sigma_max * sum_a (depth_a / thickness)^order inside the PEC box.
+    sigma = sigma_max * sum_a (depth_a / thickness)^order inside the PEC box,
+    or "learned" with learned = (thickness, params): the network of
+    fdtd_mlp_* updates the cells within `thickness` of a wall (naive scheme).
     Fields are exchanged as float32 (6, nz, ny, nx) arrays in component order
     Ex, Ey, Ez, Hx, Hy, Hz.
     """
 
     def __init__(self, shape_zyx, eps, dt, scheme="systolic", device=None, timeout_s=2.0,
                  steps_per_launch=0, max_source_steps=0, tile=None, storage="f32", field_scale=None,
-                 boundary="pec", absorber=None):
+                 boundary="pec", absorber=None, learned=None):
         import torch
         self._lib = load_library()
         self.shape = tuple(int(s) for s in shape_zyx)
@@ -185,7 +210,7 @@ class Sim:
         g, c, b = make_params(self.shape, dt, scheme=scheme, timeout_s=timeout_s,
                               steps_per_launch=steps_per_launch, max_source_steps=max_source_steps,
                               tile=tile, storage=storage, field_scale=field_scale, boundary=boundary,
-                              absorber=absorber)
+                              absorber=absorber, learned=self._learned_args(learned))
         self._params = (g, c, b)
         n = ctypes.c_size_t(0)
         _check(self._lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c), ctypes.byref(b),
@@ -201,6 +226,13 @@ class Sim:
                                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
                    "fdtd_create")
         self._h = h
+
+    def _learned_args(self, learned):
+        if learned is None:
+            return None
+        thickness, params = learned
+        self._model = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        return int(thickness), self._model
 
     @property
     def ncell(self):
@@ -292,3 +324,75 @@ def field_scales(fields, storage, headroom=4):
         e = int(np.floor(np.log2(m)))  # 2^e <= m < 2^(e+1)
         out.append(float(2.0 ** min(100, max(-100, e + 1 - (top - headroom)))))
     return out
+
+
+# ------------------------------------------------------------- learned boundary
+
+def mlp_param_count():
+    return int(load_library().fdtd_mlp_param_count())
+
+
+def _scratch(batch, n, device):
+    import torch
+    sz = ctypes.c_size_t(0)
+    _check(load_library().fdtd_mlp_scratch_size(int(batch), int(n), ctypes.byref(sz)), "fdtd_mlp_scratch_size")
+    return torch.empty(int(sz.value), dtype=torch.uint8, device=device)
+
+
+def mlp_forward(params, x, batch=4096):
+    """f(x) of the network for x [n, 324] (CUDA float32 tensors)."""
+    import torch
+    lib = load_library()
+    n = x.shape[0]
+    y = torch.empty((n, 6), dtype=torch.float32, device=x.device)
+    s = _scratch(batch, 0, x.device)
+    _check(lib.fdtd_mlp_forward(_ptr(params), _ptr(x), n, _ptr(y), int(batch), _ptr(s), s.numel(),
+                                ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)), "fdtd_mlp_forward")
+    return y
+
+
+def mlp_grad(params, x, y):
+    """(gradient, loss) of the mean squared error over the n samples."""
+    import torch
+    lib = load_library()
+    n = x.shape[0]
+    g = torch.empty_like(params)
+    s = _scratch(n, 0, x.device)
+    loss = ctypes.c_double(0.0)
+    _check(lib.fdtd_mlp_grad(_ptr(params), _ptr(x), _ptr(y), int(n), _ptr(g), ctypes.byref(loss), _ptr(s),
+                             s.numel(), ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)),
+           "fdtd_mlp_grad")
+    return g, loss.value
+
+
+def mlp_train(params, x, y, epochs, batch=4096, lr=1e-3, seed=0):
+    """Adam on the pairs (x, y) in place on `params`; returns the last epoch's loss."""
+    import torch
+    lib = load_library()
+    n = x.shape[0]
+    s = _scratch(batch, n, x.device)
+    loss = ctypes.c_double(0.0)
+    _check(lib.fdtd_mlp_train(_ptr(params), _ptr(x), _ptr(y), int(n), int(batch), int(epochs), float(lr),
+                              int(seed), _ptr(s), s.numel(),
+                              ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream), ctypes.byref(loss)),
+           "fdtd_mlp_train")
+    return loss.value
+
+
+def learned_record(sim, lo_xyz, hi_xyz, thickness, n_steps, per_step, seed=0):
+    """Training pairs from the reference simulation `sim` (see fdtd.h):
+    returns (x [n_steps*per_step, 324], y [.., 6]) CUDA tensors."""
+    import torch
+    lib = sim._lib
+    n = int(n_steps) * int(per_step)
+    x = torch.empty((n, 324), dtype=torch.float32, device=sim.device)
+    y = torch.empty((n, 6), dtype=torch.float32, device=sim.device)
+    sz = ctypes.c_size_t(0)
+    _check(lib.fdtd_learned_record_scratch_size(sim._h, int(per_step), ctypes.byref(sz)),
+           "fdtd_learned_record_scratch_size")
+    s = torch.empty(int(sz.value), dtype=torch.uint8, device=sim.device)
+    lo = (ctypes.c_int32 * 3)(*[int(v) for v in lo_xyz])
+    hi = (ctypes.c_int32 * 3)(*[int(v) for v in hi_xyz])
+    _check(lib.fdtd_learned_record(sim._h, lo, hi, int(thickness), int(n_steps), int(per_step), int(seed),
+                                   _ptr(x), _ptr(y), _ptr(s), s.numel()), "fdtd_learned_record")
+    return x, y

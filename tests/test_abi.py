@@ -1,6 +1,8 @@
 """The C-ABI library builds, loads and exports every symbol include/fdtd.h
 declares; host-side argument checks (no GPU compute)."""
 import ctypes
+
+import numpy as np
 import os
 import re
 
@@ -104,7 +106,18 @@ def test_boundary_option_checks(lib):
     for tile in ("31x15x8", "31x15x15", "31x7x15"):
         assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, boundary="graded", absorber=(8, 0.5, 3),
                                           tile=tile))[0] == fdtd.FDTD_ERR_UNSUPPORTED
-    assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, boundary="learned"))[0] == fdtd.FDTD_ERR_UNSUPPORTED
+    assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, boundary="learned"))[0] == fdtd.FDTD_ERR_INVALID_ARG
+    model = np.zeros(fdtd.mlp_param_count(), np.float32)
+    st, n_l = _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive", boundary="learned",
+                                         learned=(4, model)))
+    assert st == 0 and n_l > _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive"))[1]
+    # the layer update needs the previous level every step: naive scheme, FP32
+    assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, boundary="learned",
+                                      learned=(4, model)))[0] == fdtd.FDTD_ERR_UNSUPPORTED
+    assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive", storage="f16", boundary="learned",
+                                      learned=(4, model)))[0] == fdtd.FDTD_ERR_UNSUPPORTED
+    assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive", boundary="learned",
+                                      learned=(0, model)))[0] == fdtd.FDTD_ERR_INVALID_ARG
 
 
 def test_null_handle_calls_fail_cleanly(lib):

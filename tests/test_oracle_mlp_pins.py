@@ -6,9 +6,9 @@
   with tanh and W2 = W3 = 0 the network ignores its input.
 * The stencil layout puts a single non-zero field value where the layout
   says, and the centre at c*27 + 13.
-* The scale-equivariant prediction is homogeneous of degree 1.
-* A network whose last layer is zero freezes the layer cells; a layer of
-  thickness 0 leaves the plain Yee oracle.
+* The scale-equivariant correction is homogeneous of degree 1.
+* A network whose output is zero leaves the plain PEC box (the Yee oracle),
+  and so does a layer of thickness 0.
 """
 import numpy as np
 
@@ -69,13 +69,13 @@ def test_stencil_layout():
     assert mlp.stencil_inputs(cur, prev, [(4, 3, 2)])[0, 2 * 27 + 13] == 1.5
 
 
-def test_prediction_is_scale_equivariant():
+def test_correction_is_scale_equivariant():
     theta = mlp.init_params(5)
     x = np.random.default_rng(6).standard_normal((4, mlp.N_IN))
-    a = mlp.predict_update(theta, x)
+    a = mlp.correction(theta, x)
     for s in (2.0 ** -20, 3.0, 1e6):
-        assert np.allclose(mlp.predict_update(theta, s * x), s * a, rtol=1e-12, atol=0)
-    assert np.array_equal(mlp.predict_update(theta, np.zeros((1, mlp.N_IN))), np.zeros((1, 6)))
+        assert np.allclose(mlp.correction(theta, s * x), s * a, rtol=1e-12, atol=0)
+    assert np.array_equal(mlp.correction(theta, np.zeros((1, mlp.N_IN))), np.zeros((1, 6)))
 
 
 def test_layer_cells_and_degenerate_networks():
@@ -84,15 +84,30 @@ def test_layer_cells_and_degenerate_networks():
     assert len(cells) == 10 * 11 * 12 - 6 * 7 * 8
     eps = wl.random_eps(shape, 7)
     f0 = wl.random_fields(shape, 7)
-    # last layer zero: the layer cells keep their initial values
-    p = mlp.unpack(mlp.init_params(8))
-    p["W3"][:] = 0.0
-    cur, _ = mlp.learned_run(shape, eps, f0, 5, mlp.pack(p), thickness=2, dt=DT)
-    sel = (slice(None), cells[:, 2], cells[:, 1], cells[:, 0])
-    assert np.array_equal(cur[sel], np.asarray(f0, np.float64)[sel])
-    # thickness 0: the plain oracle
-    cur, _ = mlp.learned_run(shape, eps, f0, 5, mlp.init_params(9), thickness=0, dt=DT)
     o = YeeOracle(shape, DT, eps, quantize_ce_f32=True)
     o.set_fields(f0)
     o.step(5)
+    # zero output layer: the plain PEC box
+    p = mlp.unpack(mlp.init_params(8))
+    p["W3"][:] = 0.0
+    cur, _ = mlp.learned_run(shape, eps, f0, 5, mlp.pack(p), thickness=2, dt=DT)
     assert np.array_equal(cur, o.fields())
+    # thickness 0: the plain box too
+    cur, _ = mlp.learned_run(shape, eps, f0, 5, mlp.init_params(9), thickness=0, dt=DT)
+    assert np.array_equal(cur, o.fields())
+    # a non-zero network changes exactly the tangential values on the faces:
+    # E on the low faces, H on the high ones
+    cur, _ = mlp.learned_run(shape, eps, f0, 1, mlp.init_params(9), thickness=2, dt=DT)
+    o1 = YeeOracle(shape, DT, eps, quantize_ce_f32=True)
+    o1.set_fields(f0)
+    o1.step(1)
+    changed = cur != o1.fields()
+    nz, ny, nx = shape
+    expect = np.zeros_like(changed)
+    expect[1:3, :, :, 0] = True       # Ey, Ez at x = 0
+    expect[[0, 2], :, 0, :] = True    # Ex, Ez at y = 0
+    expect[0:2, 0, :, :] = True       # Ex, Ey at z = 0
+    expect[4:6, :, :, nx - 1] = True  # Hy, Hz at x = nx-1
+    expect[[3, 5], :, ny - 1, :] = True
+    expect[3:5, nz - 1, :, :] = True
+    assert not changed[~expect].any() and changed[expect].mean() > 0.9
