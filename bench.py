@@ -336,6 +336,8 @@ def run_sweep(args):
                 row["systolic_gcups"] = measure(shape, "systolic", "f32", steps, eps)[0]
             print(json.dumps(row), flush=True)
         return 0
+    if args.sweep == "config4":
+        return run_config4(device, stream, measure)
     # sizes: the Si/SiO2 workload at 128^3 .. 1024^3, three storage formats
     steps = args.steps_per_call if args.steps_per_call != STEPS_PER_CALL else 1000
     for n in (128, 256, 512, 768, 1024):
@@ -353,6 +355,70 @@ def run_sweep(args):
                                   "stream_bound_gcups": load_peaks()[0] / (12.0 * eb),
                                   "stream_frac": g / (load_peaks()[0] / (12.0 * eb))}), flush=True)
             torch.cuda.empty_cache()
+    return 0
+
+
+def run_config4(device, stream, measure):
+    """384^3 Si/SiO2 with a Gaussian-modulated pulse (centre wavelength 20,
+    50% bandwidth): the 32-cell graded absorber (sigma_max 0.5, order 3) with
+    both schedules, against the 4-cell learned boundary (graded base 0.3 and
+    a network trained here, on the GPU, on 48^3 thick-absorber runs) for the
+    same physical interior (328^3 = 320^3 + 2 x 4 layer cells); then the
+    reflection errors of the 48^3 experiment against the thick absorber."""
+    import torch
+    from paper_2502_20610_gb300 import fdtd
+    from paper_2502_20610_gb300 import learned
+    from paper_2502_20610_gb300 import workloads as wl
+    t0 = time.time()
+    setup = learned.Setup(n=48, thickness=4, pad=32, absorber=(32, 0.5, 3), base_sigma=0.3)
+    x, y = learned.record(setup, seed=1, runs=3, sources_per_run=3, steps=250, per_step=1000, noise=0.05)
+    params, loss = learned.train(x, y, epochs=30, batch=4096, lr=1e-3)
+    t_train = time.time() - t0
+    theta = params.cpu().numpy()
+    del x, y
+    torch.cuda.empty_cache()
+    e_l, trace = learned.reflection(setup, "learned", theta, seed=99, steps=300)
+    e_b, _ = learned.reflection(setup, "thin", seed=99, steps=300, ref_fields=trace)
+    e_t, _ = learned.reflection(setup, "thin", seed=99, steps=300, ref_fields=trace, sigma=0.5)
+    e_p, _ = learned.reflection(setup, "pec", seed=99, steps=300, ref_fields=trace)
+    del trace
+    torch.cuda.empty_cache()
+    out = {"config": "config4", "train_seconds": t_train, "train_loss": loss,
+           "reflection_error_vs_32cell_absorber": {"learned_4cell": e_l, "base_layer_alone": e_b,
+                                                   "graded_4cell_sigma0.5": e_t, "pec": e_p,
+                                                   "domain": "48^3 + 2x32 pad, eps 2.1, 300 steps"}}
+    steps = 500
+    for n, kind in ((384, "absorber32"), (328, "learned4")):
+        shape = (n, n, n)
+        eps = wl.si_sio2_eps(shape, 1)
+        J = wl.gaussian_pulse_source(steps, wl.DT_DEFAULT, wavelength=WAVELENGTH)
+        src = (2, n // 2, n // 2, n // 2)
+        schemes = ("systolic", "naive") if kind == "absorber32" else ("naive",)
+        for scheme in schemes:
+            kw = dict(boundary="graded", absorber=(32, 0.5, 3)) if kind == "absorber32" else \
+                dict(boundary="learned", learned=(4, theta, 0.3, 3))
+            sim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme=scheme, device=device, max_source_steps=steps,
+                           steps_per_launch=min(steps, 1024), **kw)
+            sim.add_source(*src, J)
+            sim.step(20)
+            sim.sync()
+            sim.set_current_step(0)
+            start = torch.cuda.Event(enable_timing=True)
+            end = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            sim.step(steps)
+            end.record(stream)
+            end.synchronize()
+            sim.sync()
+            t = start.elapsed_time(end) / 1e3
+            finite = bool(torch.isfinite(sim.read_fields()).all())
+            sim.close()
+            interior = 320 ** 3
+            out[f"{kind}_{scheme}"] = {"grid": n, "gcups": n ** 3 * steps / t / 1e9,
+                                       "interior_gcups_320cube": interior * steps / t / 1e9,
+                                       "seconds": t, "steps": steps, "finite": finite}
+            torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -385,7 +451,7 @@ def main():
     ap.add_argument("--tile", default=None, help="systolic tile shape, e.g. 31x15x15 (default: library's)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"], help="field storage format")
     ap.add_argument("--no-16bit", action="store_true", help="skip the FP16/BF16 storage context lines")
-    ap.add_argument("--sweep", default=None, choices=["fig1", "sizes"],
+    ap.add_argument("--sweep", default=None, choices=["fig1", "sizes", "config4"],
                     help="print size-sweep lines instead of the benchmark line")
     ap.add_argument("--sweep-max-log2", type=int, default=28, help="fig1: largest grid, log2 of cells")
     args = ap.parse_args()

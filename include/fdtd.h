@@ -84,22 +84,26 @@ typedef struct {
 
 /* Boundary inside the PEC box.
  *   FDTD_BOUNDARY_PEC: none.
- *   FDTD_BOUNDARY_GRADED_ABSORBER: a conducting layer (the lossy structure
- *     field of Sec. 4) of `thickness` cells at every wall,
- *     sigma = sigma_max * sum_a (depth_a / thickness)^poly_order with depth_a
+ *   FDTD_BOUNDARY_GRADED_ABSORBER: conducting cells (the lossy structure
+ *     field of Sec. 4): a layer of `thickness` cells at every wall with
+ *     sigma = sigma_max * sum_a (depth_a / thickness)^poly_order, depth_a
  *     = thickness - i inside the low layer, i - (N-1-thickness) inside the
- *     high one; the E update becomes E <- ca E + cb (curl H - J) with
+ *     high one; or, if `model` is not NULL, any conductivity: `model` is
+ *     then host nx*ny*nz doubles sigma >= 0 (copied; the profile fields are
+ *     ignored).  The E update becomes E <- ca E + cb (curl H - J) with
  *     ca = (1 - g)/(1 + g), cb = (dt/eps)/(1 + g), g = sigma dt/(2 eps),
  *     formed in FP64 and rounded to FP32 per cell.  Systolic scheme: the
  *     default 31x15x12 tile only.
- *   FDTD_BOUNDARY_LEARNED: every cell takes the Yee step of the PEC box,
- *     then the cells within `thickness` of a wall add the correction of the
- *     network `model` (host, fdtd_mlp_param_count() floats, copied; layout
- *     at fdtd_mlp_*) computed from the 3x3x3 stencils of the state at steps
- *     n and n-1 (the state before the first step, and after
- *     fdtd_write_fields, has S^{-1} = 0) to the values the PEC walls get
- *     wrong: tangential E on a cell of a low face, tangential H on a cell of
- *     a high face.  A zero network is the PEC box.
+ *   FDTD_BOUNDARY_LEARNED: a layer of `thickness` cells at every wall with
+ *     the graded conductivity above (sigma_max, poly_order; sigma_max = 0:
+ *     none) whose termination is learned: every cell takes the Yee step of
+ *     the box with its PEC walls, then each cell on a face adds the
+ *     correction of the network `model` (host, fdtd_mlp_param_count()
+ *     floats, copied; layout at fdtd_mlp_*) computed from the 3x3x3
+ *     stencils of the state at steps n and n-1 (the state before the first
+ *     step, and after fdtd_write_fields, has S^{-1} = 0) to the values the
+ *     PEC walls get wrong: tangential E on a low face, tangential H on a
+ *     high face.  A zero network leaves the graded layer on PEC walls.
  *     Naive scheme and FP32 storage only (the update needs the whole previous
  *     level every step, which the systolic tiles do not keep). */
 typedef struct {

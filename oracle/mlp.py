@@ -148,11 +148,14 @@ def layer_cells(shape_zyx, thickness):
 
 
 def learned_run(shape, eps, fields0, steps, theta, thickness=4, sources=(), dt=None, quantize=True,
-                prev0=None):
-    """FP64 learned-boundary run: the Yee oracle steps every cell, then the
-    layer cells add the network's correction.  Returns (S^n, S^{n-1})."""
+                prev0=None, sigma=None):
+    """FP64 learned-boundary run: the Yee oracle (conductivity `sigma` per
+    cell if given: the layer's base) steps every cell, then the layer cells
+    add the network's correction.  Returns (S^n, S^{n-1})."""
     from .yee import YeeOracle
     o = YeeOracle(shape, dt, eps, quantize_ce_f32=quantize)
+    if sigma is not None:
+        o.set_eps_sigma(eps, sigma, quantize)
     o.set_fields(fields0)
     for (c, i, j, k, J) in sources:
         o.add_source(c, i, j, k, J)

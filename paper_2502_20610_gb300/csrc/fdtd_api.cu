@@ -40,6 +40,13 @@ struct Layout {
 
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Does the E update have a conductivity term?  The graded absorber, and the
+// learned layer with a graded base (sigma_max > 0).
+bool conducts(const fdtd_boundary &b)
+{
+    return b.kind == FDTD_BOUNDARY_GRADED_ABSORBER || (b.kind == FDTD_BOUNDARY_LEARNED && b.sigma_max > 0.0);
+}
+
 // Cells within distance t of a wall (min over axes of the distance to the
 // nearest face < t): the total minus the inner box.
 long long cells_within(const fdtd_grid &g, int t)
@@ -97,13 +104,13 @@ bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, const fdtd_boundary &
     }
     L.ce = off;
     off = align_up(off + sizeof(float) * (size_t)n);
-    L.ca = off;  // E decay of conducting cells (absorber)
-    if (b.kind == FDTD_BOUNDARY_GRADED_ABSORBER) off = align_up(off + sizeof(float) * (size_t)n);
+    L.ca = off;  // E decay of conducting cells (absorber, or the learned layer's base)
+    if (conducts(b)) off = align_up(off + sizeof(float) * (size_t)n);
     L.nlayer = L.nband = 0;
     L.params = L.prev = L.layer = L.band = L.pred = off;
     if (b.kind == FDTD_BOUNDARY_LEARNED) {
-        L.nlayer = cells_within(g, b.thickness);
-        L.nband = cells_within(g, b.thickness + 1);
+        L.nlayer = cells_within(g, 1);  // the faces carry the network's corrections
+        L.nband = cells_within(g, 2);   // their stencils reach one cell further
         L.params = off;
         off = align_up(off + sizeof(float) * (size_t)mlpnet::NPARAM);
         L.prev = off;
@@ -174,15 +181,19 @@ fdtd_status check_args(const fdtd_grid *g, const fdtd_coeffs *c, const fdtd_boun
     for (int a = 0; a < 3; ++a)
         if (c->cluster[a] > 1) return FDTD_ERR_UNSUPPORTED;
     if (b->kind < FDTD_BOUNDARY_PEC || b->kind > FDTD_BOUNDARY_LEARNED) return FDTD_ERR_INVALID_ARG;
-    if (b->kind == FDTD_BOUNDARY_GRADED_ABSORBER) {
+    if (b->kind == FDTD_BOUNDARY_GRADED_ABSORBER && !b->model) {
         if (b->thickness < 1 || !(b->sigma_max >= 0.0) || !std::isfinite(b->sigma_max) || b->poly_order < 0 ||
             b->poly_order > 16)
             return FDTD_ERR_INVALID_ARG;
+    }
+    if (b->kind == FDTD_BOUNDARY_GRADED_ABSORBER) {
         // the register kernel's 31 x 15 x 12 tile is the one built with the lossy update
         if (c->scheme == FDTD_SCHEME_SYSTOLIC && pick_variant(*c) != 2) return FDTD_ERR_UNSUPPORTED;
     }
     if (b->kind == FDTD_BOUNDARY_LEARNED) {
-        if (b->thickness < 1 || !b->model) return FDTD_ERR_INVALID_ARG;
+        if (b->thickness < 1 || !b->model || !(b->sigma_max >= 0.0) || !std::isfinite(b->sigma_max) ||
+            b->poly_order < 0 || b->poly_order > 16)
+            return FDTD_ERR_INVALID_ARG;
         // the layer update needs the whole previous level every step: the
         // naive scheme, FP32 fields
         if (c->scheme != FDTD_SCHEME_NAIVE || c->storage != FDTD_STORAGE_F32) return FDTD_ERR_UNSUPPORTED;
@@ -205,6 +216,15 @@ double graded_sigma_at(const fdtd_grid &g, const fdtd_boundary &b, int i, int j,
         if (d > 0) s += std::pow((double)d / L, b.poly_order);
     }
     return b.sigma_max * s;
+}
+
+// Conductivity of cell (i,j,k): the caller's per-cell array (absorber with a
+// model), else the graded profile.
+double sigma_at(const fdtd_grid &g, const fdtd_boundary &b, int i, int j, int k)
+{
+    if (b.kind == FDTD_BOUNDARY_GRADED_ABSORBER && b.model)
+        return ((const double *)b.model)[i + (size_t)g.nx * ((size_t)j + (size_t)g.ny * k)];
+    return graded_sigma_at(g, b, i, j, k);
 }
 
 // Skewed-tile schedule.  Tile (I,J,K) covers sigma in [A, A+n) with
@@ -447,6 +467,11 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     const long long n = (long long)grid->nx * grid->ny * grid->nz;
     for (long long p = 0; p < n; ++p)
         if (!(eps[p] > 0.0) || !std::isfinite(eps[p])) return FDTD_ERR_INVALID_ARG;
+    if (boundary->kind == FDTD_BOUNDARY_GRADED_ABSORBER && boundary->model) {
+        const double *sg = (const double *)boundary->model;
+        for (long long p = 0; p < n; ++p)
+            if (!(sg[p] >= 0.0) || !std::isfinite(sg[p])) return FDTD_ERR_INVALID_ARG;
+    }
 
     fdtd_sim *h = new (std::nothrow) fdtd_sim();
     if (!h) return FDTD_ERR_INVALID_ARG;
@@ -458,7 +483,7 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     h->L = L;
     for (int k = 0; k < 6; ++k) h->f[k] = h->ws + L.fields[k];
     h->ce = (float *)(h->ws + L.ce);
-    h->ca = boundary->kind == FDTD_BOUNDARY_GRADED_ABSORBER ? (float *)(h->ws + L.ca) : nullptr;
+    h->ca = conducts(*boundary) ? (float *)(h->ws + L.ca) : nullptr;
     const bool learned = boundary->kind == FDTD_BOUNDARY_LEARNED;
     h->params = learned ? (float *)(h->ws + L.params) : nullptr;
     h->prev = learned ? (float *)(h->ws + L.prev) : nullptr;
@@ -508,7 +533,7 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
             for (int i = 0; i < grid->nx; ++i) {
                 const size_t p = (size_t)i + (size_t)grid->nx * ((size_t)j + (size_t)grid->ny * k);
                 if (h->ca) {
-                    const double g = graded_sigma_at(*grid, *boundary, i, j, k) * coeffs->dt / (2.0 * eps[p]);
+                    const double g = sigma_at(*grid, *boundary, i, j, k) * coeffs->dt / (2.0 * eps[p]);
                     ce[p] = (float)((coeffs->dt / eps[p]) / (1.0 + g));
                     ca[p] = (float)((1.0 - g) / (1.0 + g));
                 } else {
@@ -531,8 +556,8 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ctrl, 0, 64 * sizeof(int), h->stream);
     std::vector<int> lcells, bcells;
     if (e == cudaSuccess && learned) {
-        list_cells_within(*grid, boundary->thickness, lcells);
-        list_cells_within(*grid, boundary->thickness + 1, bcells);
+        list_cells_within(*grid, 1, lcells);
+        list_cells_within(*grid, 2, bcells);
         e = cudaMemcpyAsync(h->params, boundary->model, sizeof(float) * mlpnet::NPARAM, cudaMemcpyDefault, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->prev, 0, L.layer - L.prev, h->stream);
         if (e == cudaSuccess && !lcells.empty())
@@ -586,7 +611,7 @@ fdtd_status fdtd_add_source(fdtd_handle h, int32_t component, int32_t i, int32_t
     const long long idx = i + (long long)h->L.pitch * (j + (long long)h->g.ny * k);
     // the cell's cb (dt/eps unless it conducts)
     double c = h->c.dt / h->eps_host[(size_t)dense];
-    if (h->ca) c /= 1.0 + graded_sigma_at(h->g, h->b, i, j, k) * h->c.dt / (2.0 * h->eps_host[(size_t)dense]);
+    if (h->ca) c /= 1.0 + sigma_at(h->g, h->b, i, j, k) * h->c.dt / (2.0 * h->eps_host[(size_t)dense]);
     std::vector<float> amp((size_t)std::max<int64_t>(n_steps, 1));
     for (int64_t n = 0; n < n_steps; ++n) amp[(size_t)n] = (float)(-c * J[n]);
     float *dst = h->src_tab + (size_t)h->src.n * (size_t)h->L.source_steps;

@@ -135,8 +135,10 @@ def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
                 steps_per_launch=0, max_source_steps=0, boundary="pec", tile=None, field_scale=None,
                 absorber=None, learned=None):
     """absorber: (thickness L, sigma_max, order m) of the graded layer when
-    boundary == "graded"; learned: (thickness, params) when boundary ==
-    "learned" (params: float32 numpy array, kept alive by the caller)."""
+    boundary == "graded", or a float64 array of per-cell conductivity (kept
+    alive by the caller); learned: (thickness, params[, sigma_max, order])
+    when boundary == "learned" (params: float32 numpy array, kept alive by
+    the caller; sigma_max > 0 adds a graded base over the layer)."""
     nz, ny, nx = (int(s) for s in shape_zyx)
     g = Grid(nx, ny, nz)
     c = Coeffs()
@@ -154,11 +156,15 @@ def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
             c.tile[a] = int(t[a])
     b = Boundary()
     b.kind = BOUNDARY[boundary]
-    if absorber is not None:
+    if isinstance(absorber, np.ndarray):
+        b.model = absorber.ctypes.data
+    elif absorber is not None:
         b.thickness, b.sigma_max, b.poly_order = int(absorber[0]), float(absorber[1]), int(absorber[2])
     if learned is not None:
         b.thickness = int(learned[0])
         b.model = learned[1].ctypes.data
+        if len(learned) > 2:
+            b.sigma_max, b.poly_order = float(learned[2]), int(learned[3])
     return g, c, b
 
 
@@ -207,6 +213,9 @@ class Sim:
         self.scheme = scheme
         self.storage = storage
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if absorber is not None and not isinstance(absorber, tuple):
+            self._sigma = np.ascontiguousarray(np.broadcast_to(np.asarray(absorber, np.float64), self.shape))
+            absorber = self._sigma
         g, c, b = make_params(self.shape, dt, scheme=scheme, timeout_s=timeout_s,
                               steps_per_launch=steps_per_launch, max_source_steps=max_source_steps,
                               tile=tile, storage=storage, field_scale=field_scale, boundary=boundary,
@@ -230,9 +239,8 @@ class Sim:
     def _learned_args(self, learned):
         if learned is None:
             return None
-        thickness, params = learned
-        self._model = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
-        return int(thickness), self._model
+        self._model = np.ascontiguousarray(np.asarray(learned[1], dtype=np.float32))
+        return (int(learned[0]), self._model) + tuple(learned[2:])
 
     @property
     def ncell(self):

@@ -4,10 +4,11 @@ FDTD_BOUNDARY_LEARNED).  Orchestration only; every arithmetic step runs in
 libfdtd's CUDA kernels.
 
 Set-up (the benchmark spec (4)): the learned boundary replaces a thick graded
-absorber.  A reference domain is the learned domain D (n^3 cells) surrounded
-by `pad` more cells whose outer `absorber` cells conduct (graded, order 3);
-the network learns, for the cells of D's outer `thickness` cells, the
-reference run's next state from the stencils of the last two states with
+absorber.  A reference domain is the learned domain D (n^3 cells, its outer
+`thickness` cells a graded base layer) surrounded by `pad` more cells whose
+outer `absorber` cells conduct (graded, order 3); the network learns, for
+D's face cells, the correction from D's own Yee step (PEC walls) to the
+reference run's next state, from the stencils of the last two states with
 everything outside D read as 0 -- exactly what it will see when D stands
 alone with the learned layer at its walls.
 
@@ -26,13 +27,29 @@ from . import workloads as wl
 DT = wl.DT_DEFAULT
 
 
-class Setup:
-    """Geometry of a learned-boundary experiment (all sizes in cells)."""
+def graded_profile(n, thickness, sigma_max, order):
+    """sigma_max * sum_a (depth_a / thickness)^order on an n^3 box, depth_a =
+    thickness - i inside the low layer, i - (n-1-thickness) inside the high
+    one (the library's graded absorber profile), as float64 (n, n, n)."""
+    i = np.arange(n)
+    d = np.where(i < thickness, thickness - i, np.where(i >= n - thickness, i - (n - 1 - thickness), 0))
+    w = np.where(d > 0, (d / thickness) ** order, 0.0)
+    return sigma_max * (w[:, None, None] + w[None, :, None] + w[None, None, :])
 
-    def __init__(self, n=48, thickness=4, pad=32, absorber=(32, 0.5, 3), eps_bg=2.1):
+
+class Setup:
+    """Geometry of a learned-boundary experiment (all sizes in cells).
+
+    The learned domain D is n^3 with a `thickness`-cell layer at its walls:
+    graded conductivity `base_sigma` (order 3) whose PEC termination the
+    network corrects.  The reference is D, layer included, inside `pad`
+    more cells whose outer `absorber` cells conduct (the thick absorber)."""
+
+    def __init__(self, n=48, thickness=4, pad=32, absorber=(32, 0.5, 3), eps_bg=2.1, base_sigma=0.3):
         self.n, self.thickness, self.pad = n, thickness, pad
         self.absorber = absorber
         self.eps_bg = eps_bg
+        self.base_sigma = base_sigma
         self.N = n + 2 * pad
 
     @property
@@ -43,22 +60,33 @@ class Setup:
     def hi(self):
         return (self.pad + self.n,) * 3
 
-    def ref_sim(self, scheme="systolic", max_source_steps=0):
-        shape = (self.N,) * 3
-        return fdtd.Sim(shape, self.eps_bg, DT, scheme=scheme, boundary="graded", absorber=self.absorber,
-                        max_source_steps=max_source_steps)
+    def ref_sigma(self, with_layer=True):
+        sig = graded_profile(self.N, *self.absorber)
+        if with_layer and self.base_sigma > 0:
+            p, n = self.pad, self.n
+            sig[p:p + n, p:p + n, p:p + n] += graded_profile(n, self.thickness, self.base_sigma, 3)
+        return sig
 
-    def sim(self, kind, params=None, max_source_steps=0):
-        """The n^3 domain with boundary kind "learned", "pec" or "thin" (a graded
-        absorber of the learned layer's thickness)."""
+    def ref_sim(self, scheme="systolic", max_source_steps=0, with_layer=True):
+        """The reference domain; with_layer=False is the judge: the thick
+        absorber alone."""
+        shape = (self.N,) * 3
+        return fdtd.Sim(shape, self.eps_bg, DT, scheme=scheme, boundary="graded",
+                        absorber=self.ref_sigma(with_layer), max_source_steps=max_source_steps)
+
+    def sim(self, kind, params=None, max_source_steps=0, sigma=None):
+        """The n^3 domain with boundary kind "learned", "pec" or "thin": a
+        graded absorber of the layer's thickness with peak conductivity
+        `sigma` (default: the learned boundary's base, i.e. the learned layer
+        without its network)."""
         shape = (self.n,) * 3
         if kind == "learned":
             return fdtd.Sim(shape, self.eps_bg, DT, scheme="naive", boundary="learned",
-                            learned=(self.thickness, params), max_source_steps=max_source_steps)
+                            learned=(self.thickness, params, self.base_sigma, 3), max_source_steps=max_source_steps)
         if kind == "thin":
+            s = self.base_sigma if sigma is None else sigma
             return fdtd.Sim(shape, self.eps_bg, DT, scheme="naive", boundary="graded",
-                            absorber=(self.thickness, self.absorber[1], self.absorber[2]),
-                            max_source_steps=max_source_steps)
+                            absorber=(self.thickness, s, 3), max_source_steps=max_source_steps)
         return fdtd.Sim(shape, self.eps_bg, DT, scheme="naive", max_source_steps=max_source_steps)
 
 
@@ -118,7 +146,7 @@ def train(x, y, epochs=20, batch=4096, lr=1e-3, seed=0, init_seed=0):
     return params, loss
 
 
-def reflection(setup, kind, params=None, seed=99, steps=400, ref_fields=None):
+def reflection(setup, kind, params=None, seed=99, steps=400, ref_fields=None, sigma=None):
     """Relative error energy of boundary `kind` against the thick absorber
     over `steps` steps of a seeded pulse; returns (error, reference trace)
     where the trace (the reference's interior fields per step) can be
@@ -128,7 +156,7 @@ def reflection(setup, kind, params=None, seed=99, steps=400, ref_fields=None):
     t = setup.thickness
     inner = slice(t, setup.n - t)
     if ref_fields is None:
-        ref = setup.ref_sim(scheme="naive", max_source_steps=steps)
+        ref = setup.ref_sim(scheme="naive", max_source_steps=steps, with_layer=False)
         for (c, x, y, z, J) in src:
             ref.add_source(c, x + setup.pad, y + setup.pad, z + setup.pad, J)
         p0, p1 = setup.pad + t, setup.pad + setup.n - t
@@ -137,7 +165,7 @@ def reflection(setup, kind, params=None, seed=99, steps=400, ref_fields=None):
             ref.step(1)
             ref_fields.append(ref.read_fields()[:, p0:p1, p0:p1, p0:p1].double())
         ref.close()
-    sim = setup.sim(kind, params, max_source_steps=steps)
+    sim = setup.sim(kind, params, max_source_steps=steps, sigma=sigma)
     for (c, x, y, z, J) in src:
         sim.add_source(c, x, y, z, J)
     num = den = 0.0

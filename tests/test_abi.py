@@ -118,6 +118,13 @@ def test_boundary_option_checks(lib):
                                       learned=(4, model)))[0] == fdtd.FDTD_ERR_UNSUPPORTED
     assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive", boundary="learned",
                                       learned=(0, model)))[0] == fdtd.FDTD_ERR_INVALID_ARG
+    assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive", boundary="learned",
+                                      learned=(4, model, -0.1, 3)))[0] == fdtd.FDTD_ERR_INVALID_ARG
+    st, n_b = _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive", boundary="learned",
+                                         learned=(4, model, 0.3, 3)))
+    assert st == 0 and n_b > n_l  # the base layer's ca array
+    sig = np.zeros(shape)
+    assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, boundary="graded", absorber=sig))[0] == 0
 
 
 def test_null_handle_calls_fail_cleanly(lib):

@@ -110,7 +110,9 @@ def test_recorded_pairs_are_normalised_stencils(cuda_device):
             assert np.abs(y[s * 40 + q] - dy[best]).max() < 1e-5 * max(1.0, np.abs(cand_n[best]).max())
 
 
-def test_learned_step_matches_fp64_oracle(cuda_device):
+@pytest.mark.parametrize("base", [0.0, 0.4])
+def test_learned_step_matches_fp64_oracle(cuda_device, base):
+    from oracle.yee import graded_sigma
     shape = (20, 22, 24)
     eps = wl.random_eps(shape, 10)
     f0 = wl.random_fields(shape, 10)
@@ -119,31 +121,37 @@ def test_learned_step_matches_fp64_oracle(cuda_device):
     theta = mlp.pack(p)
     th32 = theta.astype(np.float32)
     src = [(2, 12, 11, 10, wl.sine_source(12, DT))]
-    sim = fdtd.Sim(shape, eps, DT, scheme="naive", boundary="learned", learned=(4, th32), max_source_steps=12)
+    sim = fdtd.Sim(shape, eps, DT, scheme="naive", boundary="learned", learned=(4, th32, base, 3),
+                   max_source_steps=12)
     sim.write_fields(torch.as_tensor(np.asarray(f0, np.float32)).cuda())
     sim.add_source(*src[0])
     sim.step(12)
     got = sim.read_fields().cpu().numpy()
     sim.close()
     ref, _ = mlp.learned_run(shape, eps, np.asarray(f0, np.float32).astype(np.float64), 12,
-                             th32.astype(np.float64), thickness=4, sources=src, dt=DT)
+                             th32.astype(np.float64), thickness=4, sources=src, dt=DT,
+                             sigma=graded_sigma(shape, 4, base, 3) if base > 0 else None)
     err = rel_l2_per_field(got, ref)
     assert max(err.values()) < 1e-4, err
 
 
 def test_learned_layer_beats_pec_and_a_thin_absorber(cuda_device):
-    setup = learned.Setup(n=48, thickness=4, pad=32, absorber=(32, 0.5, 3))
-    # pulses plus broadband initial noise: without the fine-grained patterns
-    # the closed loop meets patterns the network never saw and can grow them
+    # the 4-cell learned boundary (graded base, learned termination), trained
+    # on pulses plus broadband initial noise (without the fine-grained
+    # patterns the closed loop can meet patterns the network never saw and
+    # grow them), judged against the 32-cell absorber
+    setup = learned.Setup(n=48, thickness=4, pad=32, absorber=(32, 0.5, 3), base_sigma=0.3)
     x, y = learned.record(setup, seed=1, runs=3, sources_per_run=3, steps=250, per_step=1000, noise=0.05)
     assert torch.isfinite(x).all() and torch.isfinite(y).all()
     params, loss = learned.train(x, y, epochs=30, batch=4096, lr=1e-3)
     assert np.isfinite(loss)
     theta = params.cpu().numpy()
     e_learned, trace = learned.reflection(setup, "learned", theta, seed=99, steps=300)
+    e_base, _ = learned.reflection(setup, "thin", seed=99, steps=300, ref_fields=trace)
+    e_thin, _ = learned.reflection(setup, "thin", seed=99, steps=300, ref_fields=trace, sigma=0.5)
     e_pec, _ = learned.reflection(setup, "pec", seed=99, steps=300, ref_fields=trace)
-    e_thin, _ = learned.reflection(setup, "thin", seed=99, steps=300, ref_fields=trace)
-    print(f"reflection error vs the 32-cell absorber: learned {e_learned:.3e}, "
-          f"4-cell graded {e_thin:.3e}, PEC {e_pec:.3e}; training loss {loss:.3e}")
+    print(f"reflection error vs the 32-cell absorber: learned {e_learned:.3e}, its base alone {e_base:.3e}, "
+          f"4-cell graded (sigma 0.5) {e_thin:.3e}, PEC {e_pec:.3e}; training loss {loss:.3e}")
+    assert e_learned < 0.5 * e_base        # what the network adds to its own base
+    assert e_learned < 0.5 * e_thin        # and against the thick absorber cut to 4 cells
     assert e_learned < e_pec
-    assert e_learned < e_thin
