@@ -282,6 +282,39 @@ fdtd_status fdtd_learned_record(fdtd_handle h, const int32_t lo[3], const int32_
 fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *d_fields, const float *d_coef,
                                        double dt, int64_t n_steps, void *stream);
 
+/* Adjoint gradient (inverse design; the paper motivates fast FDTD with it,
+ * Sec. 1).  Objective: the overlap of Ez on the plane k = k0 with a mode
+ * profile, squared and summed over the last `window` steps:
+ *     L = sum_{n = N-window+1}^{N} O_n^2,  O_n = sum_{i,j} m(i,j) Ez^n(i,j,k0).
+ * dL/deps is the exact derivative of the discrete map (the transposed Yee
+ * step run backwards in time from step N, with dt/eps taken as dt/eps):
+ *     dL/deps_p = -(1/eps_p) sum_{n<N} sum_a lambda_{E,a}^{n+1}(p) (E^{n+1} - E^n)_a(p),
+ * accumulated in FP64 on the GPU. */
+typedef struct {
+    int32_t k0;            /* output plane (z index) */
+    const float *d_mode;   /* device, nx*ny floats m(i,j), x fastest */
+    int32_t window;        /* 1 <= window <= n_steps */
+} fdtd_overlap_objective;
+
+/* Scratch of fdtd_adjoint_gradient: ceil(n_steps/checkpoint_every) + 1 field
+ * states, the adjoint state, checkpoint_every + 1 E states of the box, and
+ * n_steps + 1 doubles.  Errors: INVALID_ARG (box outside the grid). */
+fdtd_status fdtd_adjoint_scratch_size(fdtd_handle h, int64_t n_steps, int32_t checkpoint_every,
+                                      const int32_t box_lo[3], const int32_t box_hi[3], size_t *bytes);
+
+/* Advance h by n_steps from its current state (its scheme and sources),
+ * return L in *loss (host, may be NULL) and dL/deps of the cells of the box
+ * [box_lo, box_hi) (x y z) in d_grad (device doubles, box cells x fastest).
+ * The forward pass keeps a checkpoint every checkpoint_every steps; the
+ * reverse sweep recomputes each segment from its checkpoint (keeping only
+ * the box's E) and steps the adjoint back over it.  On return h holds the
+ * state after n_steps.  FP32 storage and PEC walls only (UNSUPPORTED
+ * otherwise).  Synchronous.  Errors: INVALID_ARG, UNSUPPORTED, OOM (scratch
+ * too small), TIMEOUT, CUDA, STATE. */
+fdtd_status fdtd_adjoint_gradient(fdtd_handle h, const fdtd_overlap_objective *obj, int64_t n_steps,
+                                  int32_t checkpoint_every, const int32_t box_lo[3], const int32_t box_hi[3],
+                                  double *d_grad, double *loss, void *d_scratch, size_t scratch_bytes);
+
 #ifdef __cplusplus
 }
 #endif

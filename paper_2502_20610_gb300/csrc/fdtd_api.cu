@@ -1,6 +1,7 @@
 // Host side of libfdtd: argument checks, workspace layout, coefficients,
 // source tables, the systolic tile schedule, and kernel launches.
 // The C ABI is declared (and documented) in include/fdtd.h.
+#include "adjoint.h"
 #include "fdtd.h"
 #include "internal.h"
 #include "mlp.h"
@@ -917,6 +918,131 @@ fdtd_status fdtd_learned_record(fdtd_handle h, const int32_t lo[3], const int32_
         CK(cudaMemcpyAsync(cur, f0, 6 * arr, cudaMemcpyDeviceToDevice, h->stream));
         CK(cudaStreamSynchronize(h->stream));  // the host cell list is reused next step
     }
+    return fdtd_sync(h);
+}
+
+// ---------------------------------------------------------------- adjoint
+
+namespace {
+
+struct AdjPlan {
+    long long nseg, box_cells, arr;  // arr: floats of one field array (stride)
+    size_t ck, lam, hist, ov, total;
+};
+
+bool adj_plan(fdtd_handle h, int64_t n, int32_t K, const int32_t lo[3], const int32_t hi[3], AdjPlan &a)
+{
+    const int n3[3] = {h->g.nx, h->g.ny, h->g.nz};
+    for (int q = 0; q < 3; ++q)
+        if (lo[q] < 0 || hi[q] > n3[q] || hi[q] <= lo[q]) return false;
+    a.arr = (long long)(h->L.fields[1] - h->L.fields[0]) / 4;
+    a.nseg = (n + K - 1) / K;
+    a.box_cells = (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+    size_t off = 0;
+    a.ck = off;  // checkpoints 0 .. nseg-1 and the final state
+    off = align_up(off + sizeof(float) * 6 * (size_t)a.arr * (size_t)(a.nseg + 1));
+    a.lam = off;
+    off = align_up(off + sizeof(float) * 6 * (size_t)a.arr);
+    a.hist = off;
+    off = align_up(off + sizeof(float) * 3 * (size_t)a.box_cells * (size_t)(K + 1));
+    a.ov = off;
+    off = align_up(off + sizeof(double) * (size_t)(n + 1));
+    a.total = off;
+    return true;
+}
+
+} // namespace
+
+fdtd_status fdtd_adjoint_scratch_size(fdtd_handle h, int64_t n_steps, int32_t checkpoint_every,
+                                      const int32_t box_lo[3], const int32_t box_hi[3], size_t *bytes)
+{
+    if (!h || !bytes || !box_lo || !box_hi || n_steps < 1 || checkpoint_every < 1) return FDTD_ERR_INVALID_ARG;
+    AdjPlan a;
+    if (!adj_plan(h, n_steps, checkpoint_every, box_lo, box_hi, a)) return FDTD_ERR_INVALID_ARG;
+    *bytes = a.total;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_adjoint_gradient(fdtd_handle h, const fdtd_overlap_objective *obj, int64_t n_steps,
+                                  int32_t checkpoint_every, const int32_t box_lo[3], const int32_t box_hi[3],
+                                  double *d_grad, double *loss, void *d_scratch, size_t scratch_bytes)
+{
+    if (!h || !obj || !obj->d_mode || !box_lo || !box_hi || !d_grad || !d_scratch || n_steps < 1 ||
+        checkpoint_every < 1 || obj->k0 < 0 || obj->k0 >= h->g.nz || obj->window < 1 || obj->window > n_steps)
+        return FDTD_ERR_INVALID_ARG;
+    // the transposed step is that of the lossless FP32 Yee map with PEC walls
+    if (h->c.storage != FDTD_STORAGE_F32 || h->ca || h->params) return FDTD_ERR_UNSUPPORTED;
+    if (h->failed) return FDTD_ERR_STATE;
+    AdjPlan a;
+    if (!adj_plan(h, n_steps, checkpoint_every, box_lo, box_hi, a)) return FDTD_ERR_INVALID_ARG;
+    if (scratch_bytes < a.total) return FDTD_ERR_OOM;
+    const int K = checkpoint_every;
+    const long long N = n_steps, W = obj->window;
+    char *base = (char *)d_scratch;
+    float *ck = (float *)(base + a.ck), *lam = (float *)(base + a.lam), *hist = (float *)(base + a.hist);
+    double *ov = (double *)(base + a.ov);
+    float *f0 = (float *)h->f[0];
+    const size_t state_bytes = sizeof(float) * 6 * (size_t)a.arr;
+    auto slot = [&](long long s) { return ck + 6 * (size_t)a.arr * (size_t)s; };
+    AdjGeo g{h->g.nx, h->g.ny, h->g.nz, h->L.pitch, a.arr};
+    const int lo[3] = {box_lo[0], box_lo[1], box_lo[2]}, hi[3] = {box_hi[0], box_hi[1], box_hi[2]};
+    const long long step0 = h->step;
+    cudaStream_t st = h->stream;
+    const float dt = (float)h->c.dt;
+    fdtd_status rs;
+
+    // forward: checkpoints every K steps, the overlaps of the window's steps
+    CK(cudaMemsetAsync(ov, 0, sizeof(double) * (size_t)(N + 1), st));
+    CK(cudaMemsetAsync(d_grad, 0, sizeof(double) * (size_t)a.box_cells, st));
+    long long n = 0;
+    while (n < N) {
+        if (n % K == 0) CK(cudaMemcpyAsync(slot(n / K), f0, state_bytes, cudaMemcpyDeviceToDevice, st));
+        const long long next_ck = (n / K + 1) * K;
+        const long long upto = std::min(N, next_ck);
+        if (upto <= N - W) {  // no overlap needed before the window
+            if ((rs = fdtd_step(h, upto - n)) != FDTD_OK) return rs;
+            n = upto;
+            continue;
+        }
+        if ((rs = fdtd_step(h, 1)) != FDTD_OK) return rs;
+        ++n;
+        if (n > N - W) CK(adjoint_overlap(g, f0 + 2 * a.arr, obj->k0, obj->d_mode, ov + n, st));
+    }
+    CK(cudaMemcpyAsync(slot(a.nseg), f0, state_bytes, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> O((size_t)(N + 1));
+    CK(cudaMemcpyAsync(O.data(), ov, sizeof(double) * (size_t)(N + 1), cudaMemcpyDeviceToHost, st));
+    if ((rs = fdtd_sync(h)) != FDTD_OK) return rs;
+    double L = 0.0;
+    for (long long q = N - W + 1; q <= N; ++q) L += O[(size_t)q] * O[(size_t)q];
+    if (loss) *loss = L;
+
+    // reverse sweep, segment by segment: recompute the box's E from the
+    // checkpoint, then step the adjoint back over the segment
+    CK(cudaMemsetAsync(lam, 0, state_bytes, st));
+    const long long bc = a.box_cells;
+    auto amp = [&](long long q) { return q > N - W ? 2.0 * O[(size_t)q] : 0.0; };
+    // lambda^N = dg_N/dx^N: the adjoint source of step N alone
+    CK(adjoint_e(g, lam, 0.f, obj->k0, obj->d_mode, amp(N), st));
+    for (long long s = a.nseg - 1; s >= 0; --s) {
+        const long long s0 = s * K, s1 = std::min(N, s0 + K);
+        CK(cudaMemcpyAsync(f0, slot(s), state_bytes, cudaMemcpyDeviceToDevice, st));
+        h->step = step0 + s0;
+        CK(adjoint_box_copy(g, f0, lo, hi, hist, st));
+        for (long long q = s0 + 1; q <= s1; ++q) {
+            if ((rs = fdtd_step(h, 1)) != FDTD_OK) return rs;
+            CK(adjoint_box_copy(g, f0, lo, hi, hist + 3 * (size_t)bc * (size_t)(q - s0), st));
+        }
+        for (long long q = s1 - 1; q >= s0; --q) {
+            // lambda holds lambda^{q+1}: gradient, then lambda^q
+            CK(adjoint_h(g, lam, h->ce, lo, hi, hist + 3 * (size_t)bc * (size_t)(q + 1 - s0),
+                         hist + 3 * (size_t)bc * (size_t)(q - s0), dt, d_grad, st));
+            CK(adjoint_e(g, lam, dt, obj->k0, obj->d_mode, amp(q), st));
+            h->launches += 2;
+        }
+    }
+    // leave the simulation at step n_steps
+    CK(cudaMemcpyAsync(f0, slot(a.nseg), state_bytes, cudaMemcpyDeviceToDevice, st));
+    h->step = step0 + N;
     return fdtd_sync(h);
 }
 

@@ -26,7 +26,7 @@ EXPORTS = ("fdtd_workspace_size", "fdtd_create", "fdtd_add_source", "fdtd_write_
            "fdtd_set_current_step", "fdtd_launch_count", "fdtd_status_string", "fdtd_destroy",
            "fdtd_debug_set", "fdtd_systolic_step_noalloc", "fdtd_mlp_param_count", "fdtd_mlp_scratch_size",
            "fdtd_mlp_forward", "fdtd_mlp_grad", "fdtd_mlp_train", "fdtd_learned_record_scratch_size",
-           "fdtd_learned_record")
+           "fdtd_learned_record", "fdtd_adjoint_scratch_size", "fdtd_adjoint_gradient")
 
 
 class Grid(ctypes.Structure):
@@ -43,6 +43,10 @@ class Coeffs(ctypes.Structure):
 class Boundary(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("thickness", ctypes.c_int32), ("sigma_max", ctypes.c_double),
                 ("poly_order", ctypes.c_int32), ("model", ctypes.c_void_p)]
+
+
+class OverlapObjective(ctypes.Structure):
+    _fields_ = [("k0", ctypes.c_int32), ("d_mode", ctypes.c_void_p), ("window", ctypes.c_int32)]
 
 
 class FdtdError(RuntimeError):
@@ -107,6 +111,12 @@ def load_library(path=LIB_PATH):
                                    ctypes.POINTER(ctypes.c_double)]
     lib.fdtd_learned_record_scratch_size.restype = st
     lib.fdtd_learned_record_scratch_size.argtypes = [P, I32, ctypes.POINTER(SZ)]
+    lib.fdtd_adjoint_scratch_size.restype = st
+    lib.fdtd_adjoint_scratch_size.argtypes = [P, I64, I32, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                              ctypes.POINTER(SZ)]
+    lib.fdtd_adjoint_gradient.restype = st
+    lib.fdtd_adjoint_gradient.argtypes = [P, ctypes.POINTER(OverlapObjective), I64, I32, ctypes.POINTER(I32),
+                                          ctypes.POINTER(I32), P, ctypes.POINTER(ctypes.c_double), P, SZ]
     lib.fdtd_learned_record.restype = st
     lib.fdtd_learned_record.argtypes = [P, ctypes.POINTER(I32), ctypes.POINTER(I32), I32, I32, I32, ctypes.c_uint64,
                                         P, P, P, SZ]
@@ -404,3 +414,29 @@ def learned_record(sim, lo_xyz, hi_xyz, thickness, n_steps, per_step, seed=0):
     _check(lib.fdtd_learned_record(sim._h, lo, hi, int(thickness), int(n_steps), int(per_step), int(seed),
                                    _ptr(x), _ptr(y), _ptr(s), s.numel()), "fdtd_learned_record")
     return x, y
+
+
+# ---------------------------------------------------------------- adjoint
+
+def adjoint_gradient(sim, k0, mode, window, n_steps, box_lo, box_hi, checkpoint_every=100):
+    """Advance `sim` by n_steps and return (L, dL/deps of the box) for the
+    overlap objective of fdtd.h: L = sum over the last `window` steps of
+    (sum m(i,j) Ez(i,j,k0))^2.  mode: CUDA float32 (ny, nx); box corners in
+    (x, y, z); the gradient is a CUDA float64 tensor (nz, ny, nx) of the box."""
+    import torch
+    lib = sim._lib
+    lo = (ctypes.c_int32 * 3)(*[int(v) for v in box_lo])
+    hi = (ctypes.c_int32 * 3)(*[int(v) for v in box_hi])
+    sz = ctypes.c_size_t(0)
+    _check(lib.fdtd_adjoint_scratch_size(sim._h, int(n_steps), int(checkpoint_every), lo, hi, ctypes.byref(sz)),
+           "fdtd_adjoint_scratch_size")
+    scratch = torch.empty(int(sz.value), dtype=torch.uint8, device=sim.device)
+    mode = mode.to(device=sim.device, dtype=torch.float32).contiguous()
+    shape = tuple(int(hi[a] - lo[a]) for a in (2, 1, 0))
+    grad = torch.empty(shape, dtype=torch.float64, device=sim.device)
+    obj = OverlapObjective(int(k0), mode.data_ptr(), int(window))
+    loss = ctypes.c_double(0.0)
+    _check(lib.fdtd_adjoint_gradient(sim._h, ctypes.byref(obj), int(n_steps), int(checkpoint_every), lo, hi,
+                                     _ptr(grad), ctypes.byref(loss), _ptr(scratch), scratch.numel()),
+           "fdtd_adjoint_gradient")
+    return loss.value, grad
