@@ -338,6 +338,8 @@ def run_sweep(args):
         return 0
     if args.sweep == "config4":
         return run_config4(device, stream, measure)
+    if args.sweep == "config5":
+        return run_config5(device)
     # sizes: the Si/SiO2 workload at 128^3 .. 1024^3, three storage formats
     steps = args.steps_per_call if args.steps_per_call != STEPS_PER_CALL else 1000
     for n in (128, 256, 512, 768, 1024):
@@ -422,6 +424,67 @@ def run_config4(device, stream, measure):
     return 0
 
 
+def config5_problem(scheme="systolic"):
+    """200 x 200 x 100 grid (eps 2.1), a 64 x 64 x 20 design box of seeded
+    uniform eps in [2.1, 12.1] at the centre, a CW Jz dipole (wavelength 20)
+    below it, the overlap of Ez on the plane z = 80 with a seeded Gaussian
+    mode profile over the last 350 steps of 4000, checkpoints every 100."""
+    from paper_2502_20610_gb300 import adjoint as gadj
+    from paper_2502_20610_gb300 import workloads as wl
+    nx, ny, nz = 200, 200, 100
+    lo, hi = (68, 68, 40), (132, 132, 60)
+    steps = 4000
+    u = np.asarray(wl.uniform_pm1(11, 64 * 64 * 20)).reshape(20, 64, 64)
+    eps_box = 2.1 + 10.0 * (0.5 + 0.5 * u)
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    noise = np.asarray(wl.uniform_pm1(12, nx * ny)).reshape(ny, nx)
+    mode = np.exp(-((ii - 100.0) ** 2 + (jj - 100.0) ** 2) / (2 * 10.0 ** 2)) * (1.0 + 0.2 * noise)
+    src = (2, 100, 100, 15, wl.sine_source(steps, wl.DT_DEFAULT, WAVELENGTH))
+    p = gadj.Problem((nz, ny, nx), 2.1, lo, hi, src, k0=80, mode=mode, n_steps=steps, window=350,
+                     checkpoint_every=100, scheme=scheme)
+    return p, eps_box
+
+
+def run_config5(device):
+    """Config 5 at full size: the adjoint gradient's cost, and its
+    directional derivative against a central difference of the objective
+    along a seeded +-1 direction over the whole design box."""
+    import torch
+    from paper_2502_20610_gb300 import fdtd
+    from paper_2502_20610_gb300 import workloads as wl
+    p, eps_box = config5_problem()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L, g = p.run(eps_box)
+    t_adj = time.perf_counter() - t0
+    # forward alone, same schedule
+    sim = fdtd.Sim(p.shape, p.eps_with(eps_box), wl.DT_DEFAULT, scheme="systolic", max_source_steps=p.n_steps,
+                   steps_per_launch=1024)
+    sim.add_source(*p.source)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.step(p.n_steps)
+    sim.sync()
+    t_fwd = time.perf_counter() - t0
+    sim.close()
+    v = np.sign(np.asarray(wl.uniform_pm1(13, eps_box.size)).reshape(eps_box.shape))
+    out = {"config": "config5", "grid_xyz": [200, 200, 100], "design_box": [64, 64, 20], "steps": p.n_steps,
+           "checkpoint_every": p.checkpoint_every, "L": L, "seconds_gradient": t_adj, "seconds_forward": t_fwd,
+           "gradient_over_forward": t_adj / t_fwd,
+           "forward_gcups": 200 * 200 * 100 * p.n_steps / t_fwd / 1e9,
+           "grad_abs_max": float(g.abs().max()), "grad_norm": float(g.norm())}
+    dd = float((g.cpu().numpy() * v).sum())
+    for h in (0.2, 0.05):
+        lp, _ = p.run(eps_box + h * v)
+        lm, _ = p.run(eps_box - h * v)
+        fd = (lp - lm) / (2 * h)
+        out[f"directional_fd_h{h}"] = fd
+        out[f"directional_rel_err_h{h}"] = abs(fd - dd) / abs(dd)
+    out["directional_adjoint"] = dd
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def time_calls(sim, n_calls, stream):
     import torch
     start = torch.cuda.Event(enable_timing=True)
@@ -451,7 +514,7 @@ def main():
     ap.add_argument("--tile", default=None, help="systolic tile shape, e.g. 31x15x15 (default: library's)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"], help="field storage format")
     ap.add_argument("--no-16bit", action="store_true", help="skip the FP16/BF16 storage context lines")
-    ap.add_argument("--sweep", default=None, choices=["fig1", "sizes", "config4"],
+    ap.add_argument("--sweep", default=None, choices=["fig1", "sizes", "config4", "config5"],
                     help="print size-sweep lines instead of the benchmark line")
     ap.add_argument("--sweep-max-log2", type=int, default=28, help="fig1: largest grid, log2 of cells")
     args = ap.parse_args()
