@@ -27,6 +27,9 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     size_t fields[6], ce, ca, stage, src, progress, tiles, ctrl, total;
+    size_t xface;      // register kernel's x-face buffer (6 components)
+    long long xfs;     // its elements per component
+    int nyp;           // its y extent padded to 16 bytes
     // learned boundary: network, previous state, layer and band cell lists,
     // layer predictions
     size_t params, prev, layer, band, pred;
@@ -125,6 +128,14 @@ bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, const fdtd_boundary &
     }
     L.stage = off;
     if (c.storage != FDTD_STORAGE_F32) off = align_up(off + sizeof(float) * (size_t)g.nx * g.ny * g.nz);
+    L.nyp = (g.ny + q - 1) / q * q;
+    L.xfs = 0;
+    L.xface = off;
+    if (c.scheme == FDTD_SCHEME_SYSTOLIC && pick_variant(c) >= 2) {
+        const size_t per = align_up((size_t)L.eb * (size_t)g.nx * g.nz * L.nyp);
+        L.xfs = (long long)(per / L.eb);
+        off += 6 * per;
+    }
     L.source_steps = c.max_source_steps > 0 ? c.max_source_steps : DEFAULT_SOURCE_STEPS;
     L.src = off;
     off = align_up(off + sizeof(float) * (size_t)FDTD_MAX_SOURCES * (size_t)L.source_steps);
@@ -304,7 +315,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 }
 
 bool encode_shell_maps(CUtensorMap tm[3][8], void *fbase, long long fstride, const float *ce, const float *ca,
-                       int storage, int nx, int ny, int nz, int pitch, int nr)
+                       int storage, int nx, int ny, int nz, int pitch, int nr, void *xf, long long xfs, int nyp)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || fstride <= 0) return false;
@@ -322,9 +333,21 @@ bool encode_shell_maps(CUtensorMap tm[3][8], void *fbase, long long fstride, con
                            : (void *)(a == 6 ? ce : ca);
         const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
         for (int s = 0; s < 3; ++s) {
-            CUresult r = enc(&tm[s][a], dt, 3, base, dims, strides, box[s], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            CUresult r;
+            if (s == 2 && a < 6) {
+                // lower x shell of a field: from the x-face buffer, y innermost:
+                // dims {ny, nz, nx}, box {16 + xa, nr, 1}
+                const cuuint64_t xd[3] = {(cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nx};
+                const cuuint64_t xs[2] = {(cuuint64_t)nyp * eb, (cuuint64_t)nyp * (cuuint64_t)nz * eb};
+                const cuuint32_t xb[3] = {16u + xa, (cuuint32_t)nr, 1u};
+                void *xbase = (char *)xf + (size_t)a * (size_t)xfs * eb;
+                r = enc(&tm[s][a], dt, 3, xbase, xd, xs, xb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            } else {
+                r = enc(&tm[s][a], dt, 3, base, dims, strides, box[s], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            }
             if (r != CUDA_SUCCESS) return false;
         }
     }
@@ -589,7 +612,8 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
         if (L.variant >= 2) {
             const long long fstride = (long long)(L.fields[1] - L.fields[0]) / L.eb;
             if (!encode_shell_maps(h->tm, h->f[0], fstride, h->ce, h->ca, coeffs->storage, grid->nx, grid->ny,
-                                   grid->nz, L.pitch, systolic_reg_rows(L.variant - 2)))
+                                   grid->nz, L.pitch, systolic_reg_rows(L.variant - 2), h->ws + L.xface, L.xfs,
+                                   L.nyp))
                 return fail(FDTD_ERR_UNSUPPORTED);
         }
         fdtd_status st = upload_tiles(h, 0, 0);
@@ -720,6 +744,9 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         p.fbase = (float *)h->f[0];
         p.fstride = (long long)(h->L.fields[1] - h->L.fields[0]) / h->L.eb;
         p.sc = h->sc;
+        p.xf = (float *)(h->ws + h->L.xface);
+        p.xfs = h->L.xfs;
+        p.nyp = h->L.nyp;
         p.gx = h->L.gx;
         p.gy = h->L.gy;
         p.gz = h->L.gz;

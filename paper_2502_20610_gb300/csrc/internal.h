@@ -77,6 +77,12 @@ struct SysLaunch {
     float *fbase;            // f[c] == fbase + c*fstride elements for c in 0..5 when the
     long long fstride;       // arrays sit at a uniform stride (else fstride == 0)
     Scales sc;               // storage scales (16-bit formats)
+    // top x faces of the register kernel: component c of cell (x,y,z) at
+    // xf + c*xfs + x*(nz*nyp) + z*nyp + y elements, so a face (fixed x) is
+    // stored and loaded along y; the field arrays never carry them
+    float *xf;
+    long long xfs;
+    int nyp;
     int gx, gy, gz;          // tile grid over skewed space sigma = p + t
     int T;                   // steps of this launch
     unsigned epoch;          // progress values of this launch are epoch + k
@@ -95,12 +101,14 @@ struct SysLaunch {
     CUtensorMap tm[3][8];
 };
 
-// Encode the 21 shell maps of the register kernel with `nr` z rows per
-// column: the six fields (storage format `storage`, at fbase + c*fstride
-// elements) and the FP32 coefficient array ce, all with rows of `pitch`
-// elements.  Returns false on failure.
+// Encode the shell maps of the register kernel with `nr` z rows per column:
+// lower z and y shells of the six fields (storage format `storage`, at
+// fbase + c*fstride elements) and of the FP32 coefficients ce (and ca), rows
+// of `pitch` elements; the lower x shell of the fields from the x-face
+// buffer xf (see SysLaunch), of the coefficients from ce / ca.  Returns false
+// on failure.
 bool encode_shell_maps(CUtensorMap tm[3][8], void *fbase, long long fstride, const float *ce, const float *ca,
-                       int storage, int nx, int ny, int nz, int pitch, int nr);
+                       int storage, int nx, int ny, int nz, int pitch, int nr, void *xf, long long xfs, int nyp);
 int systolic_reg_rows(int k);
 
 size_t systolic_smem_bytes(int variant);

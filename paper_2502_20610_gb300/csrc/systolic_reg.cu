@@ -69,7 +69,9 @@ struct RegTile {
     static constexpr int XA = 16 / EB, SW = 32 + XA;
     static constexpr int ZB = RY * SW;                                  // z shell box {SW,16,1}: [y][x]
     static constexpr int YB = (NR * SW * EB + 127) / 128 * 128 / EB;   // y shell box {SW,1,NR}: [z][x], padded
-    static constexpr int XB = NR * 16 * XA;                            // x shell box {XA,16,NR}: [z][y][x]
+    // x shell box of the fields, from the x-face buffer {16 + XA, NR, 1}: [z][y]
+    static constexpr int SWY = 16 + XA;
+    static constexpr int XB = (NR * SWY * EB + 127) / 128 * 128 / EB;
     static constexpr int XAC = 4, SWC = 36;
     static constexpr int ZBC = RY * SWC, YBC = (NR * SWC * 4 + 127) / 128 * 32, XBC = NR * 16 * XAC;
     static_assert((ZB * EB) % 128 == 0 && (XB * EB) % 128 == 0 && (YB * EB) % 128 == 0, "boxes stay 128-byte aligned");
@@ -78,7 +80,7 @@ struct RegTile {
     static constexpr int CST_F = ZBC + YBC + XBC;          // coefficient staging floats
     static constexpr int NCOEF = LOSSY ? 2 : 1;   // FP32 coefficient arrays: cb (dt/eps), ca
     static constexpr unsigned TMA_BYTES =
-        6u * EB * (RY * SW + NR * SW + NR * 16 * XA) + NCOEF * 4u * (RY * SWC + NR * SWC + NR * 16 * XAC);
+        6u * EB * (RY * SW + NR * SW + NR * SWY) + NCOEF * 4u * (RY * SWC + NR * SWC + NR * 16 * XAC);
     static constexpr int CR = 16;                 // coefficient ring rows (>= NR, power of 2)
     static constexpr int CE_F = RY * CR * 32;
     static_assert(CR >= NR, "coefficient ring holds the whole column");
@@ -174,23 +176,37 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #define SC(c) P.sc.s[c]
 #define IS(c) P.sc.is[c]
 #define RND(v, c) S::rnd(v, SC(c), IS(c))
+// the inverse scale of field f, picked without a dynamically indexed
+// parameter array
+#define ISF(f) ((f) == 0 ? IS(0) : (f) == 1 ? IS(1) : (f) == 2 ? IS(2) : (f) == 3 ? IS(3) : (f) == 4 ? IS(4) : IS(5))
+// the staged top x face of the step whose box corner is (pbx, pby, pbz)
+#define STORE_XFACE(pbx, pby, pbz)                                                                  \
+    do {                                                                                            \
+        const int qx_ = (pbx) + TX - 1, qy_ = (pby) + q_y;                                          \
+        if (q_y < TY && (unsigned)qx_ < (unsigned)P.nx && (unsigned)qy_ < (unsigned)P.ny) {         \
+            const int wv_ = qy_ & (R::RY - 1);                                                      \
+            _Pragma("unroll") for (int k_ = 0; k_ < NPASS; ++k_) {                                  \
+                const int pr_ = q_p + 32 * k_;                                                      \
+                const int f_ = pr_ / NZ, zr_ = pr_ - f_ * NZ, qz_ = (pbz) + zr_;                    \
+                if (pr_ < NPAIR && (unsigned)qz_ < (unsigned)P.nz)                                  \
+                    XF[f_ * XFS + qx_ * XFX + qz_ * XFZ + qy_] =                                    \
+                        S::enc(XO[(wv_ * 6 + f_) * NZ + zr_], ISF(f_));                             \
+            }                                                                                       \
+        }                                                                                           \
+    } while (0)
 #define STORE6(g, i)                                                                          \
     do {                                                                                      \
         F0[g] = S::enc(ex[i], IS(0)); F1[g] = S::enc(ey[i], IS(1)); F2[g] = S::enc(ez[i], IS(2)); \
         F3[g] = S::enc(hx[i], IS(3)); F4[g] = S::enc(hy[i], IS(4)); F5[g] = S::enc(hz[i], IS(5)); \
     } while (0)
 
-    // Cooperative x-shell load and top x-face store: thread bits pick the
-    // entry (row = tid & 15, field = (tid >> 4) & 7, warp offset = tid >> 7,
-    // plus 4 per pass), so no division is needed.  Field c of the workspace
-    // is fbase + c*fstride elements.
-    const int q_row = tid & 15, q_f = (tid >> 4) & 7, q_w = tid >> 7;
-    T *const FB = reinterpret_cast<T *>(P.fbase);
-    const long long FS = P.fstride;
-    // the inverse scale of this thread's x-face field, picked without a
-    // dynamically indexed parameter array
-    const float q_is = q_f == 0 ? IS(0) : q_f == 1 ? IS(1) : q_f == 2 ? IS(2) : q_f == 3 ? IS(3)
-                     : q_f == 4 ? IS(4) : IS(5);
+    // Top x-face store into the x-face buffer, along y: thread t takes y
+    // offset t & 15 and (field, z row) pairs (t >> 4) + 32 k, so each warp
+    // writes two runs of 15 consecutive values.
+    T *const XF = reinterpret_cast<T *>(P.xf);
+    const long long XFS = P.xfs, XFZ = (long long)P.nyp, XFX = (long long)P.nyp * P.nz;
+    const int q_y = tid & 15, q_p = tid >> 4;
+    constexpr int NPAIR = 6 * NZ, NPASS = (NPAIR + 31) / 32;
 
     constexpr int CR = R::CR;
     if (tid == 0) {
@@ -239,6 +255,10 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             const int bx = Ax - iv.s, by = Ay - iv.s;
             const int px = bx + ((lane - bx) & 31), py = by + ((w - by) & (R::RY - 1));
             const bool cin = (unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny;
+            // the lower x shell column at level start-1: written by the left
+            // tiles into the x-face buffer during this launch (start >= 1), or
+            // the launch's initial state in the field arrays (start = 0)
+            const bool xshell = px == bx && iv.s > 0;
             const long long col = px + (long long)P.pitch * py;
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
@@ -246,9 +266,16 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 float c = 0.f, a = 0.f;
                 if (cin && (unsigned)pz < (unsigned)P.nz) {
                     const long long g = col + sxy * pz;
-                    ex[i] = S::dec(S::ld_cg(F0 + g), SC(0)); ey[i] = S::dec(S::ld_cg(F1 + g), SC(1));
-                    ez[i] = S::dec(S::ld_cg(F2 + g), SC(2)); hx[i] = S::dec(S::ld_cg(F3 + g), SC(3));
-                    hy[i] = S::dec(S::ld_cg(F4 + g), SC(4)); hz[i] = S::dec(S::ld_cg(F5 + g), SC(5));
+                    if (xshell) {  // the left tiles' top x face of level start-1
+                        const long long q = px * XFX + pz * XFZ + py;
+                        ex[i] = S::dec(S::ld_cg(XF + q), SC(0)); ey[i] = S::dec(S::ld_cg(XF + XFS + q), SC(1));
+                        ez[i] = S::dec(S::ld_cg(XF + 2 * XFS + q), SC(2)); hx[i] = S::dec(S::ld_cg(XF + 3 * XFS + q), SC(3));
+                        hy[i] = S::dec(S::ld_cg(XF + 4 * XFS + q), SC(4)); hz[i] = S::dec(S::ld_cg(XF + 5 * XFS + q), SC(5));
+                    } else {
+                        ex[i] = S::dec(S::ld_cg(F0 + g), SC(0)); ey[i] = S::dec(S::ld_cg(F1 + g), SC(1));
+                        ez[i] = S::dec(S::ld_cg(F2 + g), SC(2)); hx[i] = S::dec(S::ld_cg(F3 + g), SC(3));
+                        hy[i] = S::dec(S::ld_cg(F4 + g), SC(4)); hz[i] = S::dec(S::ld_cg(F5 + g), SC(5));
+                    }
                     c = __ldg(CE + g);
                     if (R::LOSSY) a = __ldg(CA + g);
                 } else {
@@ -304,32 +331,22 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     }
                 }
             }
-            if (t > iv.s && q_row < NZ && q_f < 6) {  // top x face of step t-1, staged in XO
-                const int pbx = bx + 1, pby = by + 1, pbz = bz + 1;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int wi = q_w + 4 * q;
-                    if (wi < TY) {
-                        const int wv = (pby + wi) & (R::RY - 1);
-                        const int qx = pbx + TX - 1, qy = pby + wi, qz = pbz + q_row;
-                        if (in_dom(P, qx, qy, qz))
-                            FB[q_f * FS + gidx(P, qx, qy, qz)] = S::enc(XO[(wv * 6 + q_f) * NZ + q_row], q_is);
-                    }
-                }
-            }
+            if (t > iv.s) STORE_XFACE(bx + 1, by + 1, bz + 1);  // top x face of step t-1, staged in XO
             // lower shells (level t) into shared staging: 21 bulk tensor copies
             // issued by one thread (x start rounded down to 16 bytes; zero fill
             // off the domain)
-            const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1);
+            const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1), y0 = by & ~(XA - 1);
             if (tid == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                // order this thread's view of the upwind tiles' stores (generic
+                // proxy) and of the staging area before the bulk copies
+                asm volatile("fence.proxy.async;" ::: "memory");
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_bar)),
                              "r"(R::TMA_BYTES) : "memory");
 #pragma unroll
                 for (int f = 0; f < 6; ++f) {
                     tma_box(ZST + f * R::ZB, &P.tm[0][f], x0, by - 1, bz - 1, &s_bar);
                     tma_box(YST + f * R::YB, &P.tm[1][f], x0, by - 1, bz - 1, &s_bar);
-                    tma_box(XST + f * R::XB, &P.tm[2][f], x0, by, bz - 1, &s_bar);
+                    tma_box(XST + f * R::XB, &P.tm[2][f], y0, bz - 1, bx - 1, &s_bar);
                 }
                 tma_box(ZSC, &P.tm[0][6], x0c, by - 1, bz - 1, &s_bar);
                 tma_box(YSC, &P.tm[1][6], x0c, by - 1, bz - 1, &s_bar);
@@ -367,7 +384,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 
             // D. refills from the staged shells, then publish new H rows for the
             //    warp above's E half-step
-            const int xe = (bx - 1) - x0, xec = (bx - 1) - x0c;  // x offset of the shell column in its chunk
+            const int xec = (bx - 1) - x0c;  // x offset of the coefficient shell column in its chunk
             if (w == ey_w) {  // the y shell warp takes its whole column set (level t)
                 const int xw = (bx - 1) + ((lane - bx + 1) & 31);
                 const int xl = xw - x0, xlc = xw - x0c;
@@ -390,14 +407,14 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZSC[oc];
                 if (R::LOSSY) CAs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZSA[oc];
             } else {  // the lane leaving the tile in x takes the x shell's H and coefficient
-                const T *xs = XST + dy * XA + xe;
+                const T *xs = XST + (by + dy - y0);
                 const float *xsc = XSC + dy * R::XAC + xec;
                 const float *xsa = XSA + dy * R::XAC + xec;
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
-                    hx[i] = S::dec(xs[3 * R::XB + i * 16 * XA], SC(3));
-                    hy[i] = S::dec(xs[4 * R::XB + i * 16 * XA], SC(4));
-                    hz[i] = S::dec(xs[5 * R::XB + i * 16 * XA], SC(5));
+                    hx[i] = S::dec(xs[3 * R::XB + i * R::SWY], SC(3));
+                    hy[i] = S::dec(xs[4 * R::XB + i * R::SWY], SC(4));
+                    hz[i] = S::dec(xs[5 * R::XB + i * R::SWY], SC(5));
                     CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xsc[i * 16 * R::XAC];
                     if (R::LOSSY) CAs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xsa[i * 16 * R::XAC];
                 }
@@ -464,12 +481,12 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     ey[0] = S::dec(ZST[1 * R::ZB + o], SC(1));
                     ez[0] = S::dec(ZST[2 * R::ZB + o], SC(2));
                 } else {  // the x lane takes the rest of its shell column
-                    const T *xs = XST + dy * XA + xe;
+                    const T *xs = XST + (by + dy - y0);
 #pragma unroll
                     for (int i = 0; i < NR; ++i) {
-                        ex[i] = S::dec(xs[0 * R::XB + i * 16 * XA], SC(0));
-                        ey[i] = S::dec(xs[1 * R::XB + i * 16 * XA], SC(1));
-                        ez[i] = S::dec(xs[2 * R::XB + i * 16 * XA], SC(2));
+                        ex[i] = S::dec(xs[0 * R::XB + i * R::SWY], SC(0));
+                        ey[i] = S::dec(xs[1 * R::XB + i * R::SWY], SC(1));
+                        ez[i] = S::dec(xs[2 * R::XB + i * R::SWY], SC(2));
                     }
                 }
             }
@@ -511,31 +528,29 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                         }
                     }
                 }
-            } else {
-                if (colin) {
-                    // (the top y face is stored next step by the warp holding it)
-                    if (NR - 1 >= i_lo && NR - 1 < i_hi) {  // top z face
-                        const long long g = col + sxy * (bz + NR - 2);
-                        STORE6(g, NR - 1);
-                    }
+            } else if (colin) {
+                // (the top y face is stored next step by the warp holding it)
+                if (NR - 1 >= i_lo && NR - 1 < i_hi) {  // top z face
+                    const long long g = col + sxy * (bz + NR - 2);
+                    STORE6(g, NR - 1);
                 }
-                if (ybox && dx == TX - 1) {  // top x face: staged, stored at B1 of the next step
-                    float *xo = XO + w * 6 * NZ;
+            }
+            if (ybox && dx == TX - 1) {  // top x face: staged, stored into the x-face buffer next step
+                float *xo = XO + w * 6 * NZ;
 #pragma unroll
-                    for (int k = 0; k < NZ / 4; ++k) {
-                        *reinterpret_cast<float4 *>(xo + 0 * NZ + 4 * k) =
-                            make_float4(ex[4 * k + 1], ex[4 * k + 2], ex[4 * k + 3], ex[4 * k + 4]);
-                        *reinterpret_cast<float4 *>(xo + 1 * NZ + 4 * k) =
-                            make_float4(ey[4 * k + 1], ey[4 * k + 2], ey[4 * k + 3], ey[4 * k + 4]);
-                        *reinterpret_cast<float4 *>(xo + 2 * NZ + 4 * k) =
-                            make_float4(ez[4 * k + 1], ez[4 * k + 2], ez[4 * k + 3], ez[4 * k + 4]);
-                        *reinterpret_cast<float4 *>(xo + 3 * NZ + 4 * k) =
-                            make_float4(hx[4 * k + 1], hx[4 * k + 2], hx[4 * k + 3], hx[4 * k + 4]);
-                        *reinterpret_cast<float4 *>(xo + 4 * NZ + 4 * k) =
-                            make_float4(hy[4 * k + 1], hy[4 * k + 2], hy[4 * k + 3], hy[4 * k + 4]);
-                        *reinterpret_cast<float4 *>(xo + 5 * NZ + 4 * k) =
-                            make_float4(hz[4 * k + 1], hz[4 * k + 2], hz[4 * k + 3], hz[4 * k + 4]);
-                    }
+                for (int k = 0; k < NZ / 4; ++k) {
+                    *reinterpret_cast<float4 *>(xo + 0 * NZ + 4 * k) =
+                        make_float4(ex[4 * k + 1], ex[4 * k + 2], ex[4 * k + 3], ex[4 * k + 4]);
+                    *reinterpret_cast<float4 *>(xo + 1 * NZ + 4 * k) =
+                        make_float4(ey[4 * k + 1], ey[4 * k + 2], ey[4 * k + 3], ey[4 * k + 4]);
+                    *reinterpret_cast<float4 *>(xo + 2 * NZ + 4 * k) =
+                        make_float4(ez[4 * k + 1], ez[4 * k + 2], ez[4 * k + 3], ez[4 * k + 4]);
+                    *reinterpret_cast<float4 *>(xo + 3 * NZ + 4 * k) =
+                        make_float4(hx[4 * k + 1], hx[4 * k + 2], hx[4 * k + 3], hx[4 * k + 4]);
+                    *reinterpret_cast<float4 *>(xo + 4 * NZ + 4 * k) =
+                        make_float4(hy[4 * k + 1], hy[4 * k + 2], hy[4 * k + 3], hy[4 * k + 4]);
+                    *reinterpret_cast<float4 *>(xo + 5 * NZ + 4 * k) =
+                        make_float4(hz[4 * k + 1], hz[4 * k + 2], hz[4 * k + 3], hz[4 * k + 4]);
                 }
             }
         }
@@ -558,19 +573,9 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 }
             }
         }
-        if (iv.e < P.T - 1 && q_row < NZ && q_f < 6) {
-            const int pbx = Ax - iv.e, pby = Ay - iv.e, pbz = Az - iv.e;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int wi = q_w + 4 * q;
-                if (wi < TY) {
-                    const int wv = (pby + wi) & (R::RY - 1);
-                    const int qx = pbx + TX - 1, qy = pby + wi, qz = pbz + q_row;
-                    if (in_dom(P, qx, qy, qz))
-                        FB[q_f * FS + gidx(P, qx, qy, qz)] = S::enc(XO[(wv * 6 + q_f) * NZ + q_row], q_is);
-                }
-            }
-        }
+        // the downwind tile reads the x face of every level, the launch's last
+        // one included, from the x-face buffer
+        STORE_XFACE(Ax - iv.e, Ay - iv.e, Az - iv.e);
         __syncthreads();
         if (tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.e + 1u);
     }
@@ -588,6 +593,8 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #undef IS
 #undef RND
 #undef STORE6
+#undef STORE_XFACE
+#undef ISF
 
 // 31 x 15 x 12 and 31 x 15 x 8 tiles, each for every kernel format; the
 // lossy (absorber) form for the 31 x 15 x 12 tile
