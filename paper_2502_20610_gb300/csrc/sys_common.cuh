@@ -108,6 +108,28 @@ static __device__ bool wait_level(const SysLaunch &P, const Upwind &U, unsigned 
     return __all_sync(0xffffffffu, ok);
 }
 
+// Non-blocking form of wait_level: true (in every lane) if each upwind
+// neighbour that must be waited on for level L has already published it;
+// one poll per neighbour at most.
+static __device__ bool level_ready(const SysLaunch &P, const Upwind &U, unsigned *seen, int L)
+{
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    if (lane < 3) {
+        const int a = lane;
+        const int id = a == 0 ? U.id[0] : (a == 1 ? U.id[1] : U.id[2]);
+        const int us = a == 0 ? U.s[0] : (a == 1 ? U.s[1] : U.s[2]);
+        const int ue = a == 0 ? U.e[0] : (a == 1 ? U.e[1] : U.e[2]);
+        const unsigned target = P.epoch + (unsigned)L + 1u;
+        if (id >= 0 && us <= ue + 1 && L >= us - 1 && L <= ue && seen[a] < target) {
+            const unsigned v = ld_acquire(P.progress + id);
+            if (v >= target) seen[a] = v;
+            else ok = false;
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
 __device__ __forceinline__ void publish(const SysLaunch &P, int tile, int ticket, unsigned value)
 {
     if (P.dbg_kind == 1 /* skip publish */ && ticket == P.dbg_ticket) return;

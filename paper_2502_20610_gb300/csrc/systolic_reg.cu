@@ -84,9 +84,14 @@ struct RegTile {
     static constexpr int CR = 16;                 // coefficient ring rows (>= NR, power of 2)
     static constexpr int CE_F = RY * CR * 32;
     static_assert(CR >= NR, "coefficient ring holds the whole column");
+    // staging buffers: two (the next step's shells are fetched during this
+    // step) unless the lossy form's second coefficient set leaves no room
+    static constexpr int NBUF = LOSSY_ ? 1 : 2;
+    static constexpr size_t STG_B = FST_B + sizeof(float) * NCOEF * (size_t)CST_F;  // one buffer, bytes
+    static_assert(STG_B % 128 == 0, "buffers stay 128-byte aligned");
     static constexpr size_t smem_bytes()
     {
-        return FST_B + sizeof(float) * (4 * (size_t)XE_F + XO_F + NCOEF * (size_t)(CE_F + CST_F));
+        return NBUF * STG_B + sizeof(float) * (4 * (size_t)XE_F + XO_F + NCOEF * (size_t)CE_F);
     }
 };
 
@@ -137,17 +142,12 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     constexpr int NZ = R::NZ, NR = R::NR, TX = R::TX, TY = R::TY, TZ = R::TZ;
     constexpr int SW = R::SW, XA = R::XA, SWC = R::SWC;
     extern __shared__ __align__(1024) float4 smem4[];
-    // staging boxes first: the dynamic shared memory base is 1024-byte aligned
-    T *const ZST = reinterpret_cast<T *>(smem4);  // lower z shell, 6 fields
-    T *const YST = ZST + 6 * R::ZB;               // lower y shell
-    T *const XST = YST + 6 * R::YB;               // lower x shell
-    float *const ZSC = reinterpret_cast<float *>(reinterpret_cast<char *>(smem4) + R::FST_B);  // dt/eps shells
-    float *const YSC = ZSC + R::ZBC;
-    float *const XSC = YSC + R::YBC;
-    float *const ZSA = XSC + R::XBC;       // ca shells (lossy only)
-    float *const YSA = ZSA + R::ZBC;
-    float *const XSA = YSA + R::YBC;
-    float *const XEx = (R::LOSSY ? XSA + R::XBC : ZSA);  // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
+    // staging buffers first (the dynamic shared memory base is 1024-byte
+    // aligned), each: the lower z, y and x shells of the 6 fields, then those
+    // of dt/eps (and ca); the pointers below are buffer 0's, buffer b is
+    // R::STG_B bytes further
+    char *const stg0 = reinterpret_cast<char *>(smem4);
+    float *const XEx = reinterpret_cast<float *>(stg0 + R::NBUF * R::STG_B);  // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
     float *const XEz = XEx + R::XE_F;
     float *const XHx = XEz + R::XE_F;      // [warp][row i-1][lane]: new H rows r = 0..NZ-1
     float *const XHz = XHx + R::XE_F;
@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     float *const CEs = XO + R::XO_F;       // [warp][physical z mod CR][lane]
     float *const CAs = CEs + R::CE_F;      // the same for ca (lossy only)
     __shared__ int s_ticket, s_abort;
-    __shared__ alignas(8) unsigned long long s_bar;  // staging barrier: one phase per step
+    __shared__ alignas(8) unsigned long long s_bar[2];  // staging barriers, one per buffer: one phase per fill
+    __shared__ int s_pref;                              // next step's shells issued during this one
     __shared__ unsigned s_seen[3];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -210,11 +211,45 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 
     constexpr int CR = R::CR;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    unsigned stage_phase = 0;  // completed phases of s_bar
+    // fills issued into / waited for on each buffer (every thread keeps the
+    // same counts: the issue decisions are broadcast through shared memory)
+    unsigned n_iss0 = 0, n_iss1 = 0, n_wait0 = 0, n_wait1 = 0;
+    // lower shells of level t into buffer b: 21 (lossy 24) bulk tensor copies
+    // issued by one thread (x start rounded down to 16 bytes; zero fill off
+    // the domain)
+    auto issue_shells = [&](int t, int b, int Ax, int Ay, int Az) {
+        const int bx = Ax - t, by = Ay - t, bz = Az - t;
+        const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1), y0 = by & ~(XA - 1);
+        char *sb = stg0 + (size_t)b * R::STG_B;
+        T *zst = reinterpret_cast<T *>(sb), *yst = zst + 6 * R::ZB, *xst = yst + 6 * R::YB;
+        float *zsc = reinterpret_cast<float *>(sb + R::FST_B), *ysc = zsc + R::ZBC, *xsc = ysc + R::YBC;
+        float *zsa = xsc + R::XBC, *ysa = zsa + R::ZBC, *xsa = ysa + R::YBC;
+        unsigned long long *bar = &s_bar[b];
+        // order this thread's view of the upwind tiles' stores (generic proxy)
+        // and of the staging area before the bulk copies
+        asm volatile("fence.proxy.async;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                     "r"(R::TMA_BYTES) : "memory");
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            tma_box(zst + f * R::ZB, &P.tm[0][f], x0, by - 1, bz - 1, bar);
+            tma_box(yst + f * R::YB, &P.tm[1][f], x0, by - 1, bz - 1, bar);
+            tma_box(xst + f * R::XB, &P.tm[2][f], y0, bz - 1, bx - 1, bar);
+        }
+        tma_box(zsc, &P.tm[0][6], x0c, by - 1, bz - 1, bar);
+        tma_box(ysc, &P.tm[1][6], x0c, by - 1, bz - 1, bar);
+        tma_box(xsc, &P.tm[2][6], x0c, by, bz - 1, bar);
+        if (R::LOSSY) {
+            tma_box(zsa, &P.tm[0][7], x0c, by - 1, bz - 1, bar);
+            tma_box(ysa, &P.tm[1][7], x0c, by - 1, bz - 1, bar);
+            tma_box(xsa, &P.tm[2][7], x0c, by, bz - 1, bar);
+        }
+    };
     // the tile column of this thread: registers row i <-> r = i-1
     float ex[NR], ey[NR], ez[NR], hx[NR], hy[NR], hz[NR];
 
@@ -288,8 +323,15 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
         if (iv.s > 0 && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.s);
 
         bool abort = false;
+        bool pref = false;  // this step's shells were issued during the previous step
         for (int t = iv.s; t <= iv.e; ++t) {
             const int bx = Ax - t, by = Ay - t, bz = Az - t;  // box low corner at step t
+            const int cur = R::NBUF == 2 ? (t & 1) : 0;
+            char *const sb = stg0 + (size_t)cur * R::STG_B;
+            T *const ZST = reinterpret_cast<T *>(sb), *const YST = ZST + 6 * R::ZB, *const XST = YST + 6 * R::YB;
+            float *const ZSC = reinterpret_cast<float *>(sb + R::FST_B), *const YSC = ZSC + R::ZBC;
+            float *const XSC = YSC + R::YBC, *const ZSA = XSC + R::XBC, *const YSA = ZSA + R::ZBC;
+            float *const XSA = YSA + R::YBC;
             const int dx = (lane - bx) & 31, dy = (w - by) & (R::RY - 1);
             const int px = bx + dx, py = by + dy;
             const bool xbox = dx < TX, ybox = dy < TY;
@@ -307,10 +349,16 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             }
             if (w == 0) {
                 const bool ok = wait_level(P, U, s_seen, t, ticket);
-                if (tid == 0) s_abort = !ok;
+                // may the next step's shells be fetched now?  (one poll)
+                const bool nxt = R::NBUF == 2 && ok && t + 1 <= iv.e && level_ready(P, U, s_seen, t + 1);
+                if (tid == 0) {
+                    s_abort = !ok;
+                    s_pref = nxt;
+                }
             }
             __syncthreads();  // B1
             if (s_abort) { abort = true; break; }
+            const bool pref_next = s_pref != 0;
 
             // B. the warp whose y slot leaves the tile this step is idle during
             //    the H half-step: it stores last step's top y face, which its
@@ -332,31 +380,15 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 }
             }
             if (t > iv.s) STORE_XFACE(bx + 1, by + 1, bz + 1);  // top x face of step t-1, staged in XO
-            // lower shells (level t) into shared staging: 21 bulk tensor copies
-            // issued by one thread (x start rounded down to 16 bytes; zero fill
-            // off the domain)
+            // lower shells of level t (unless fetched during the previous step),
+            // and those of level t+1 into the other buffer when they are ready
             const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1), y0 = by & ~(XA - 1);
             if (tid == 0) {
-                // order this thread's view of the upwind tiles' stores (generic
-                // proxy) and of the staging area before the bulk copies
-                asm volatile("fence.proxy.async;" ::: "memory");
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_bar)),
-                             "r"(R::TMA_BYTES) : "memory");
-#pragma unroll
-                for (int f = 0; f < 6; ++f) {
-                    tma_box(ZST + f * R::ZB, &P.tm[0][f], x0, by - 1, bz - 1, &s_bar);
-                    tma_box(YST + f * R::YB, &P.tm[1][f], x0, by - 1, bz - 1, &s_bar);
-                    tma_box(XST + f * R::XB, &P.tm[2][f], y0, bz - 1, bx - 1, &s_bar);
-                }
-                tma_box(ZSC, &P.tm[0][6], x0c, by - 1, bz - 1, &s_bar);
-                tma_box(YSC, &P.tm[1][6], x0c, by - 1, bz - 1, &s_bar);
-                tma_box(XSC, &P.tm[2][6], x0c, by, bz - 1, &s_bar);
-                if (R::LOSSY) {
-                    tma_box(ZSA, &P.tm[0][7], x0c, by - 1, bz - 1, &s_bar);
-                    tma_box(YSA, &P.tm[1][7], x0c, by - 1, bz - 1, &s_bar);
-                    tma_box(XSA, &P.tm[2][7], x0c, by, bz - 1, &s_bar);
-                }
+                if (!pref) issue_shells(t, cur, Ax, Ay, Az);
+                if (pref_next) issue_shells(t + 1, cur ^ 1, Ax, Ay, Az);
             }
+            if (!pref) (cur ? n_iss1 : n_iss0) += 1;
+            if (pref_next) (cur ? n_iss0 : n_iss1) += 1;
 
             // C. H half-step, top-down in place: H[i] <- H[i-1] - dt curl_f(E[i-1], E[i], ...)
             if (w != ey_w) {
@@ -377,8 +409,12 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     hz[i] = upd ? RND(nhz, 5) : hz[i - 1];
                 }
             }
-            if (!wait_stage(P, &s_bar, stage_phase & 1u, ticket)) s_abort = 1;
-            ++stage_phase;
+            {
+                unsigned &nw = cur ? n_wait1 : n_wait0;
+                if (!wait_stage(P, &s_bar[cur], nw & 1u, ticket)) s_abort = 1;
+                ++nw;
+            }
+            pref = pref_next;
             __syncthreads();  // the staged shells are visible
             if (s_abort) { abort = true; break; }
 
@@ -578,6 +614,12 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
         STORE_XFACE(Ax - iv.e, Ay - iv.e, Az - iv.e);
         __syncthreads();
         if (tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.e + 1u);
+    }
+    // after an abort, bulk copies may still be writing into the staging
+    // buffers: wait for them (bounded) before the CTA's shared memory goes
+    if (tid == 0) {
+        while (n_wait0 < n_iss0 && wait_stage(P, &s_bar[0], n_wait0 & 1u, -1)) ++n_wait0;
+        while (n_wait1 < n_iss1 && wait_stage(P, &s_bar[1], n_wait1 & 1u, -1)) ++n_wait1;
     }
 }
 
