@@ -409,14 +409,15 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     hz[i] = upd ? RND(nhz, 5) : hz[i - 1];
                 }
             }
+            // every thread waits on the staging barrier itself: its completion
+            // makes the copied shells visible to that thread, so no block
+            // barrier is needed here (a timeout is noticed after B2)
             {
                 unsigned &nw = cur ? n_wait1 : n_wait0;
                 if (!wait_stage(P, &s_bar[cur], nw & 1u, ticket)) s_abort = 1;
                 ++nw;
             }
             pref = pref_next;
-            __syncthreads();  // the staged shells are visible
-            if (s_abort) { abort = true; break; }
 
             // D. refills from the staged shells, then publish new H rows for the
             //    warp above's E half-step
@@ -461,6 +462,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 XHz[(w * NZ + (i - 1)) * 32 + lane] = hz[i];
             }
             __syncthreads();  // B2
+            if (s_abort) { abort = true; break; }
             if (t > iv.s && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)t);  // level t-1 done
 
             // does this thread own a point source this step?  (16-bit storage:
