@@ -514,6 +514,7 @@ def main():
     ap.add_argument("--tile", default=None, help="systolic tile shape, e.g. 31x15x15 (default: library's)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"], help="field storage format")
     ap.add_argument("--no-16bit", action="store_true", help="skip the FP16/BF16 storage context lines")
+    ap.add_argument("--no-1024", action="store_true", help="skip the 1024^3 context measurement")
     ap.add_argument("--sweep", default=None, choices=["fig1", "sizes", "config4", "config5"],
                     help="print size-sweep lines instead of the benchmark line")
     ap.add_argument("--sweep-max-log2", type=int, default=28, help="fig1: largest grid, log2 of cells")
@@ -602,6 +603,34 @@ def main():
     if not args.no_16bit and args.storage == "f32" and args.scheme == "systolic":
         narrow = [time_storage_variant(shape, eps, J, (c, i, j, k), st, device, stream) for st in ("f16", "bf16")]
 
+    # the systolic kernel at 1024^3 (same generator, 1000 steps), where the
+    # target of the metric's streaming roofline is quoted
+    big = None
+    if not args.no_1024 and args.storage == "f32" and args.scheme == "systolic" and GRID[0] == 256:
+        n, steps = 1024, 1000
+        bshape = (n, n, n)
+        beps, bJ, (bc, bi, bj, bk) = make_workload(bshape)
+        bsim = fdtd.Sim(bshape, beps, wl.DT_DEFAULT, scheme="systolic", device=device, steps_per_launch=steps,
+                        max_source_steps=bJ.size)
+        bsim.add_source(bc, bi, bj, bk, bJ)
+        bsim.step(steps)
+        bsim.sync()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        bsim.step(steps)
+        end.record(stream)
+        end.synchronize()
+        bsim.sync()
+        tb = start.elapsed_time(end) / 1e3
+        bsim.close()
+        del beps
+        torch.cuda.empty_cache()
+        peak_b, kind_b = load_peaks()
+        g = n ** 3 * steps / tb / 1e9
+        big = {"grid_xyz": [n, n, n], "steps": steps, "gcups": g, "seconds": tb,
+               "stream_frac": g / (peak_b / 48.0), "peak_kind": kind_b}
+
     if rank != 0:
         return 0
     peak, peak_kind = load_peaks()
@@ -626,8 +655,10 @@ def main():
         "stream_roofline": {"bytes_per_cell_step": 12.0 * eb,
                             "bound_gcups": peak / (12.0 * eb),
                             "frac": gcups / world / (peak / (12.0 * eb)), "peak_kind": peak_kind},
+        "dram_gbs_measured": (per_update * cells * STEPS_PER_CALL * args.steps / elapsed / 1e9) if per_update else None,
         "naive": naive,
         "storage_16bit": narrow,
+        "systolic_1024": big,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
