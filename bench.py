@@ -656,6 +656,9 @@ def main():
                             "bound_gcups": peak / (12.0 * eb),
                             "frac": gcups / world / (peak / (12.0 * eb)), "peak_kind": peak_kind},
         "dram_gbs_measured": (per_update * cells * STEPS_PER_CALL * args.steps / elapsed / 1e9) if per_update else None,
+        "paper_context": {"tcups_abstract": 0.15, "tcups_introduction": 0.18, "hardware": "1x H100",
+                          "conditions": "16-bit fields, eps and sigma, no sources, domain size not stated",
+                          "note": "context only, not this workload"},
         "naive": naive,
         "storage_16bit": narrow,
         "systolic_1024": big,
