@@ -424,26 +424,39 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
     const int ntiles = (ncells + LC - 1) / LC;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();  // previous tile done with Xt / H / rr
-        // gather: thread -> cell q = tid % 64, quarter = tid / 64 of the 324 inputs
+        // gather: thread -> cell q = tid % 64 and three of the twelve (level,
+        // component) pairs, (tid / 64) * 3 + 0..2, each a 27-cell stencil;
+        // neighbour offsets are unrolled, validity is per axis
         {
-            const int q = tid & (LC - 1), part_i = tid >> 6;
+            const int q = tid & (LC - 1), p0 = (tid >> 6) * 3;
             const int cell = tile * LC + q;
             float ss = 0.f;
             if (cell < ncells) {
                 const int x = cells[3 * cell], y = cells[3 * cell + 1], z = cells[3 * cell + 2];
-                for (int k = part_i * (NI / 4); k < (part_i + 1) * (NI / 4); ++k) {
-                    const int s = k / 162, c = (k / 27) % 6, d = k % 27;
-                    const int xx = x + d % 3 - 1, yy = y + (d / 3) % 3 - 1, zz = z + d / 9 - 1;
-                    float v = 0.f;
-                    if ((unsigned)xx < (unsigned)nx && (unsigned)yy < (unsigned)ny && (unsigned)zz < (unsigned)nz)
-                        v = (s == 0 ? cur : prev)[c * fstride + xx + (long long)pitch * yy + sxy * zz];
-                    Xt[k * LC + q] = v;
-                    ss = __fmaf_rn(v, v, ss);
+                const bool vx[3] = {x > 0, true, x + 1 < nx}, vy[3] = {y > 0, true, y + 1 < ny},
+                           vz[3] = {z > 0, true, z + 1 < nz};
+                const long long centre = x + (long long)pitch * y + sxy * z;
+#pragma unroll
+                for (int pq = 0; pq < 3; ++pq) {
+                    const int pr = p0 + pq, lev = pr / 6, comp = pr - lev * 6;
+                    const float *src = (lev == 0 ? cur : prev) + comp * fstride + centre;
+                    float *dst = Xt + (pr * 27) * LC + q;
+#pragma unroll
+                    for (int d = 0; d < 27; ++d) {
+                        const int dx = d % 3, dy = (d / 3) % 3, dz = d / 9;
+                        float v = 0.f;
+                        if (vx[dx] && vy[dy] && vz[dz]) v = src[(dx - 1) + (long long)pitch * (dy - 1) + sxy * (dz - 1)];
+                        dst[d * LC] = v;
+                        ss = __fmaf_rn(v, v, ss);
+                    }
                 }
             } else {
-                for (int k = part_i * (NI / 4); k < (part_i + 1) * (NI / 4); ++k) Xt[k * LC + q] = 0.f;
+#pragma unroll
+                for (int pq = 0; pq < 3; ++pq)
+#pragma unroll
+                    for (int d = 0; d < 27; ++d) Xt[((p0 + pq) * 27 + d) * LC + q] = 0.f;
             }
-            part[part_i * LC + q] = ss;
+            part[(tid >> 6) * LC + q] = ss;
         }
         __syncthreads();
         if (tid < LC) {
@@ -455,8 +468,10 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
         }
         __syncthreads();
         // layer 1: H1 = tanh((W1 x) / r + b1), cells tm*4.., units tn*4..
+        // (unrolled so the shared loads of later k are issued ahead)
         {
             float acc[4][4] = {};
+#pragma unroll 6
             for (int k = 0; k < NI; ++k) {
                 const float4 a = *reinterpret_cast<const float4 *>(Xt + k * LC + tm * 4);
                 const float4 w = *reinterpret_cast<const float4 *>(W1t + k * NH + tn * 4);
@@ -477,6 +492,7 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
         // layer 2
         {
             float acc[4][4] = {};
+#pragma unroll 8
             for (int k = 0; k < NH; ++k) {
                 const float4 a = *reinterpret_cast<const float4 *>(H1t + k * LC + tm * 4);
                 const float4 w = *reinterpret_cast<const float4 *>(W2t + k * NH + tn * 4);
