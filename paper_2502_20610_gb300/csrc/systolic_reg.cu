@@ -21,11 +21,20 @@
 // operations instead of ~27 shared-memory accesses.
 //
 // The slot that leaves the tile at the top in x (one lane per warp) and in y
-// (one warp) is refilled each step with the lower x / y shell: the y warp
-// loads its column rows itself (coalesced); the x columns are fetched by all
-// threads into a staging area that each x lane then reads with 16-byte
-// shared loads.  The top x face is written back the same way, one step late,
-// which is why a tile publishes level t at the second barrier of step t+1.
+// (one warp) is refilled each step with the lower x / y shell, and row -1
+// with the lower z shell.  All three shells of level t are fetched into a
+// shared staging buffer by 21 bulk tensor copies (TMA) that one thread
+// issues; with two buffers, the next step's copies go out during this step
+// as soon as the upwind tiles have published that level.  Each thread waits
+// on the buffer's mbarrier itself.
+//
+// Top faces: z and y faces go to the field arrays (the y face one step late,
+// from the warp whose y slot leaves, while it sits out the H half-step); the
+// x face is staged in shared memory and stored one step late, along y, into
+// a separate x-face buffer from which the downwind tile's x shell is
+// fetched.  A tile therefore publishes level t at the second barrier of
+// step t+1.  Two block barriers per step: after the E rows are exchanged for
+// the H half-step, and after the H rows are exchanged for the E half-step.
 //
 // Tile: 31 x 15 x NZ updated cells.  Every arithmetic step is yee_cell.cuh,
 // so the result equals the naive schedule bit for bit.
