@@ -314,42 +314,53 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-bool encode_shell_maps(CUtensorMap tm[3][8], void *fbase, long long fstride, const float *ce, const float *ca,
+bool encode_shell_maps(CUtensorMap tm[3][2], void *fbase, long long fstride, const float *ce, const float *ca,
                        int storage, int nx, int ny, int nz, int pitch, int nr, void *xf, long long xfs, int nyp)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || fstride <= 0) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    std::memset(tm, 0, sizeof(CUtensorMap) * 3 * 8);
-    for (int a = 0; a < (ca ? 8 : 7); ++a) {
-        // arrays 6, 7 are dt/eps (cb) and ca (FP32); the fields use the storage element
-        const int eb = a < 6 ? storage_bytes(storage) : 4;
+    std::memset(tm, 0, sizeof(CUtensorMap) * 3 * 2);
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const long long n = (long long)pitch * ny * nz;
+    // the coefficient arrays as a 4th dimension: cb, then ca at its own offset
+    const long long cstride_b = ca ? (long long)((const char *)ca - (const char *)ce) : 4 * n;
+    if (cstride_b <= 0 || cstride_b % 16 != 0) return false;
+    const cuuint64_t ncoef = ca ? 2 : 1;
+    for (int a = 0; a < 2; ++a) {
+        const int eb = a == 0 ? storage_bytes(storage) : 4;
         const cuuint32_t xa = 16u / (cuuint32_t)eb, sw = 32u + xa;
-        const cuuint64_t strides[2] = {(cuuint64_t)pitch * eb, (cuuint64_t)pitch * (cuuint64_t)ny * eb};
-        // lower z shell {sw,16,1}, lower y shell {sw,1,nr}, lower x shell {xa,16,nr}
-        const cuuint32_t box[3][3] = {{sw, 16, 1}, {sw, 1, (cuuint32_t)nr}, {xa, 16, (cuuint32_t)nr}};
-        void *base = a < 6 ? (void *)((char *)fbase + (size_t)a * (size_t)fstride * eb)
-                           : (void *)(a == 6 ? ce : ca);
+        const cuuint64_t nf = a == 0 ? 6 : ncoef;
+        const cuuint32_t bf = (cuuint32_t)nf;
         const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-        for (int s = 0; s < 3; ++s) {
-            CUresult r;
-            if (s == 2 && a < 6) {
-                // lower x shell of a field: from the x-face buffer, y innermost:
-                // dims {ny, nz, nx}, box {16 + xa, nr, 1}
-                const cuuint64_t xd[3] = {(cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nx};
-                const cuuint64_t xs[2] = {(cuuint64_t)nyp * eb, (cuuint64_t)nyp * (cuuint64_t)nz * eb};
-                const cuuint32_t xb[3] = {16u + xa, (cuuint32_t)nr, 1u};
-                void *xbase = (char *)xf + (size_t)a * (size_t)xfs * eb;
-                r = enc(&tm[s][a], dt, 3, xbase, xd, xs, xb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            } else {
-                r = enc(&tm[s][a], dt, 3, base, dims, strides, box[s], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            }
-            if (r != CUDA_SUCCESS) return false;
+        const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, nf};
+        const cuuint64_t strides[3] = {(cuuint64_t)pitch * eb, (cuuint64_t)pitch * (cuuint64_t)ny * eb,
+                                       a == 0 ? (cuuint64_t)fstride * eb : (cuuint64_t)cstride_b};
+        void *base = a == 0 ? fbase : (void *)ce;
+        // lower z shell {sw,16,1}, lower y shell {sw,1,nr} of every array
+        const cuuint32_t box[2][4] = {{sw, 16, 1, bf}, {sw, 1, (cuuint32_t)nr, bf}};
+        for (int s = 0; s < 2; ++s) {
+            if (enc(&tm[s][a], dt, 4, base, dims, strides, box[s], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
         }
+        CUresult r;
+        if (a == 0) {
+            // lower x shell of the fields: from the x-face buffer, y innermost:
+            // dims {ny, nz, nx, 6}, box {16 + xa, nr, 1, 6}
+            const cuuint64_t xd[4] = {(cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nx, 6};
+            const cuuint64_t xs[3] = {(cuuint64_t)nyp * eb, (cuuint64_t)nyp * (cuuint64_t)nz * eb,
+                                      (cuuint64_t)xfs * eb};
+            const cuuint32_t xb[4] = {16u + xa, (cuuint32_t)nr, 1u, 6u};
+            r = enc(&tm[2][0], dt, 4, xf, xd, xs, xb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        } else {
+            // lower x shell of the coefficients: a 16-byte x chunk {4,16,nr}
+            const cuuint32_t xb[4] = {4u, 16u, (cuuint32_t)nr, bf};
+            r = enc(&tm[2][1], dt, 4, base, dims, strides, xb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
+        if (r != CUDA_SUCCESS) return false;
     }
     return true;
 }
@@ -408,7 +419,7 @@ struct fdtd_sim {
     int dbg_kind;
     long long dbg_ticket, dbg_param, dbg_param2;
     bool failed;
-    CUtensorMap tm[3][8];  // shell maps of the register kernel
+    CUtensorMap tm[3][2];  // shell maps of the register kernel
 };
 
 namespace {

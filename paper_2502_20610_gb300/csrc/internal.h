@@ -96,18 +96,21 @@ struct SysLaunch {
     int dbg_kind;
     long long dbg_ticket, dbg_param, dbg_param2;
     SrcSet src;
-    // bulk-tensor (TMA) maps of the 6 fields, dt/eps (cb) and ca, for the
-    // register kernel's shell staging: [shape][array], shapes = lower z, y, x shell
-    CUtensorMap tm[3][8];
+    // bulk-tensor (TMA) maps of the register kernel's shell staging:
+    // [shell][0] the six fields, [shell][1] the FP32 coefficients cb (dt/eps)
+    // and, when lossy, ca, each with the array index as a 4th dimension;
+    // shells = lower z, y, x
+    CUtensorMap tm[3][2];
 };
 
 // Encode the shell maps of the register kernel with `nr` z rows per column:
 // lower z and y shells of the six fields (storage format `storage`, at
-// fbase + c*fstride elements) and of the FP32 coefficients ce (and ca), rows
-// of `pitch` elements; the lower x shell of the fields from the x-face
-// buffer xf (see SysLaunch), of the coefficients from ce / ca.  Returns false
-// on failure.
-bool encode_shell_maps(CUtensorMap tm[3][8], void *fbase, long long fstride, const float *ce, const float *ca,
+// fbase + c*fstride elements) and of the FP32 coefficients ce (and ca, at any
+// 16-byte multiple after ce), rows of `pitch` elements; the lower x shell of
+// the fields from the x-face buffer xf (see SysLaunch), of the coefficients
+// from ce / ca.  One map covers all arrays of a kind (4th dimension), so one
+// bulk copy fetches a shell of all of them.  Returns false on failure.
+bool encode_shell_maps(CUtensorMap tm[3][2], void *fbase, long long fstride, const float *ce, const float *ca,
                        int storage, int nx, int ny, int nz, int pitch, int nr, void *xf, long long xfs, int nyp);
 int systolic_reg_rows(int k);
 

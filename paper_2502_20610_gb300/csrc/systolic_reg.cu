@@ -23,20 +23,30 @@
 // The slot that leaves the tile at the top in x (one lane per warp) and in y
 // (one warp) is refilled each step with the lower x / y shell, and row -1
 // with the lower z shell.  All three shells of level t are fetched into a
-// shared staging buffer by 21 bulk tensor copies (TMA) that one thread
-// issues; with two buffers, the next step's copies go out during this step
-// as soon as the upwind tiles have published that level.  Each thread waits
-// on the buffer's mbarrier itself.
+// shared staging buffer by six bulk tensor copies (TMA): one per shell for
+// the six fields (the field index is the 4th dimension of the copy), one per
+// shell for the coefficients.  Each thread waits on the buffer's mbarrier
+// itself.
+//
+// The warp whose y slot is outside the box sits out both half-steps, so it
+// carries the tile's bookkeeping: after the second barrier it polls the
+// upwind tiles' progress once for level t+1 and, if they have published it,
+// fetches those shells into the second staging buffer, and it publishes the
+// tile's own level t-1.  Only when that poll failed (or on a tile's first
+// step) does warp 0 wait for the upwind tiles at the start of the step, and
+// thread 0 fetch the shells then.
 //
 // Top faces: z and y faces go to the field arrays (the y face one step late,
 // from the warp whose y slot leaves, while it sits out the H half-step); the
 // x face is staged in shared memory and stored one step late, along y, into
 // a separate x-face buffer from which the downwind tile's x shell is
-// fetched.  A tile therefore publishes level t at the second barrier of
-// step t+1.  Two block barriers per step: after the E rows are exchanged for
+// fetched.  A tile therefore publishes level t-1 after the second barrier of
+// step t.  Two block barriers per step: after the E rows are exchanged for
 // the H half-step, and after the H rows are exchanged for the E half-step.
 //
-// Tile: 31 x 15 x NZ updated cells.  Every arithmetic step is yee_cell.cuh,
+// Tile: 31 x 15 x NZ updated cells.  A step whose box lies inside the domain
+// and clear of the low walls (most steps of a large grid) runs both
+// half-steps with no per-cell masks.  Every arithmetic step is yee_cell.cuh,
 // so the result equals the naive schedule bit for bit.
 //
 // Storage: fields live in global memory as FP32, FP16 or BF16 (S, see
@@ -55,7 +65,7 @@ namespace {
 
 using namespace sysc;
 
-template <int NZ_, class S_, bool LOSSY_>
+template <int NZ_, class S_, bool LOSSY_, int TY_>
 struct RegTile {
     using S = S_;
     static constexpr bool LOSSY = LOSSY_;  // conducting cells: E <- ca E + cb curl H
@@ -63,7 +73,11 @@ struct RegTile {
     static constexpr int NZ = NZ_;        // updated z rows (registers 0..NZ-1)
     static constexpr int NR = NZ_ + 1;    // plus the shell row -1
     static constexpr int RY = 16, NT = 32 * RY;
-    static constexpr int TX = 31, TY = RY - 1, TZ = NZ_;
+    // TY = RY - 1: one y slot outside the box, the y shell (its warp also
+    // holds the previous step's top y row until its refill); TY = RY - 2:
+    // the previous top row has a slot (and warp) of its own
+    static constexpr int TX = 31, TY = TY_, TZ = NZ_;
+    static_assert(TY_ == RY - 1 || TY_ == RY - 2, "one or two y slots outside the box");
     static_assert(NR <= 16 && TY <= 16, "cooperative entries: row < 16, warp offset < 16");
     static_assert(NZ % 4 == 0, "top x face is staged with 16-byte stores");
     // shared memory, in floats
@@ -71,33 +85,37 @@ struct RegTile {
     static constexpr int XO_F = RY * 6 * NZ;
     // lower-shell staging, filled per step by bulk tensor copies (TMA) of
     // boxes whose x start is rounded down to 16 bytes (XA elements): SW =
-    // 32 + XA elements cover the 32-wide x window.  Fields use the storage
-    // element, the coefficient FP32 (C-suffixed sizes); every box starts on
-    // a 128-byte boundary.
+    // 32 + XA elements cover the 32-wide x window.  One copy per shell
+    // fetches all six fields ([field][...] in shared memory), one more the
+    // FP32 coefficients (C-suffixed sizes, [cb, ca][...]); sizes below are
+    // per array, in elements, and every shell's region starts on a 128-byte
+    // boundary.
     static constexpr int EB = (int)sizeof(T);
     static constexpr int XA = 16 / EB, SW = 32 + XA;
-    static constexpr int ZB = RY * SW;                                  // z shell box {SW,16,1}: [y][x]
-    static constexpr int YB = (NR * SW * EB + 127) / 128 * 128 / EB;   // y shell box {SW,1,NR}: [z][x], padded
+    static constexpr int ZB = RY * SW;        // z shell box {SW,16,1}: [y][x]
+    static constexpr int YB = NR * SW;        // y shell box {SW,1,NR}: [z][x]
     // x shell box of the fields, from the x-face buffer {16 + XA, NR, 1}: [z][y]
     static constexpr int SWY = 16 + XA;
-    static constexpr int XB = (NR * SWY * EB + 127) / 128 * 128 / EB;
+    static constexpr int XB = NR * SWY;
     static constexpr int XAC = 4, SWC = 36;
-    static constexpr int ZBC = RY * SWC, YBC = (NR * SWC * 4 + 127) / 128 * 32, XBC = NR * 16 * XAC;
-    static_assert((ZB * EB) % 128 == 0 && (XB * EB) % 128 == 0 && (YB * EB) % 128 == 0, "boxes stay 128-byte aligned");
-    static_assert((ZBC * 4) % 128 == 0 && (XBC * 4) % 128 == 0, "boxes stay 128-byte aligned");
-    static constexpr int FST_B = 6 * (ZB + YB + XB) * EB;  // field staging bytes
-    static constexpr int CST_F = ZBC + YBC + XBC;          // coefficient staging floats
+    static constexpr int ZBC = RY * SWC, YBC = NR * SWC, XBC = NR * 16 * XAC;
     static constexpr int NCOEF = LOSSY ? 2 : 1;   // FP32 coefficient arrays: cb (dt/eps), ca
+    static constexpr size_t r128(size_t b) { return (b + 127) / 128 * 128; }
+    // byte offsets of the shells within one staging buffer
+    static constexpr size_t OFF_Y = r128(6 * (size_t)ZB * EB);
+    static constexpr size_t OFF_X = OFF_Y + r128(6 * (size_t)YB * EB);
+    static constexpr size_t OFF_ZC = OFF_X + r128(6 * (size_t)XB * EB);
+    static constexpr size_t OFF_YC = OFF_ZC + r128(NCOEF * 4 * (size_t)ZBC);
+    static constexpr size_t OFF_XC = OFF_YC + r128(NCOEF * 4 * (size_t)YBC);
     static constexpr unsigned TMA_BYTES =
-        6u * EB * (RY * SW + NR * SW + NR * SWY) + NCOEF * 4u * (RY * SWC + NR * SWC + NR * 16 * XAC);
+        6u * EB * (ZB + YB + XB) + NCOEF * 4u * (ZBC + YBC + XBC);
     static constexpr int CR = 16;                 // coefficient ring rows (>= NR, power of 2)
     static constexpr int CE_F = RY * CR * 32;
     static_assert(CR >= NR, "coefficient ring holds the whole column");
     // staging buffers: two (the next step's shells are fetched during this
     // step) unless the lossy form's second coefficient set leaves no room
     static constexpr int NBUF = LOSSY_ ? 1 : 2;
-    static constexpr size_t STG_B = FST_B + sizeof(float) * NCOEF * (size_t)CST_F;  // one buffer, bytes
-    static_assert(STG_B % 128 == 0, "buffers stay 128-byte aligned");
+    static constexpr size_t STG_B = OFF_XC + r128(NCOEF * 4 * (size_t)XBC);  // one buffer, bytes
     static constexpr size_t smem_bytes()
     {
         return NBUF * STG_B + sizeof(float) * (4 * (size_t)XE_F + XO_F + NCOEF * (size_t)CE_F);
@@ -108,14 +126,16 @@ __device__ __forceinline__ float shfl_from(float v, int src) { return __shfl_syn
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-// Bulk tensor copy of one 3D box (TMA) into shared memory, completing on an
-// mbarrier; elements outside the tensor are written as zero.
+// Bulk tensor copy of one box of a 4D map (TMA: x, y, z, array) starting at
+// array 0 into shared memory, completing on an mbarrier; elements outside
+// the tensor are written as zero.
 __device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *map, int x, int y, int z,
                                         unsigned long long *bar)
 {
-    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                 " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-                 "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(0),
+                 "r"(smem_u32(bar))
                  : "memory");
 }
 
@@ -167,7 +187,11 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     float *const CAs = CEs + R::CE_F;      // the same for ca (lossy only)
     __shared__ int s_ticket, s_abort;
     __shared__ alignas(8) unsigned long long s_bar[2];  // staging barriers, one per buffer: one phase per fill
-    __shared__ int s_pref;                              // next step's shells issued during this one
+    // state of the next step's shells, decided during this one: 0 = the
+    // upwind tiles have not published them yet, 1 = published and fetched
+    // into the other buffer, 2 = published, not yet fetched (one buffer)
+    __shared__ int s_pref;
+    __shared__ unsigned s_niss[2];                      // fills issued into each buffer
     __shared__ unsigned s_seen[3];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -220,44 +244,36 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 
     constexpr int CR = R::CR;
     if (tid == 0) {
+        s_niss[0] = s_niss[1] = 0u;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[0])) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    // fills issued into / waited for on each buffer (every thread keeps the
-    // same counts: the issue decisions are broadcast through shared memory)
-    unsigned n_iss0 = 0, n_iss1 = 0, n_wait0 = 0, n_wait1 = 0;
-    // lower shells of level t into buffer b: 21 (lossy 24) bulk tensor copies
-    // issued by one thread (x start rounded down to 16 bytes; zero fill off
-    // the domain)
+    // fills waited for on each buffer (every thread waits on every fill, so
+    // every thread keeps the same counts)
+    unsigned n_wait0 = 0, n_wait1 = 0;
+    // lower shells of level t into buffer b: six bulk tensor copies issued by
+    // one thread (x start rounded down to 16 bytes; zero fill off the domain),
+    // counted in s_niss for the final drain
     auto issue_shells = [&](int t, int b, int Ax, int Ay, int Az) {
         const int bx = Ax - t, by = Ay - t, bz = Az - t;
         const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1), y0 = by & ~(XA - 1);
         char *sb = stg0 + (size_t)b * R::STG_B;
-        T *zst = reinterpret_cast<T *>(sb), *yst = zst + 6 * R::ZB, *xst = yst + 6 * R::YB;
-        float *zsc = reinterpret_cast<float *>(sb + R::FST_B), *ysc = zsc + R::ZBC, *xsc = ysc + R::YBC;
-        float *zsa = xsc + R::XBC, *ysa = zsa + R::ZBC, *xsa = ysa + R::YBC;
         unsigned long long *bar = &s_bar[b];
-        // order this thread's view of the upwind tiles' stores (generic proxy)
-        // and of the staging area before the bulk copies
-        asm volatile("fence.proxy.async;" ::: "memory");
+        // order this thread's view of the upwind tiles' global stores (generic
+        // proxy, acquired through their progress flags) before the bulk copies
+        // that read them
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                      "r"(R::TMA_BYTES) : "memory");
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            tma_box(zst + f * R::ZB, &P.tm[0][f], x0, by - 1, bz - 1, bar);
-            tma_box(yst + f * R::YB, &P.tm[1][f], x0, by - 1, bz - 1, bar);
-            tma_box(xst + f * R::XB, &P.tm[2][f], y0, bz - 1, bx - 1, bar);
-        }
-        tma_box(zsc, &P.tm[0][6], x0c, by - 1, bz - 1, bar);
-        tma_box(ysc, &P.tm[1][6], x0c, by - 1, bz - 1, bar);
-        tma_box(xsc, &P.tm[2][6], x0c, by, bz - 1, bar);
-        if (R::LOSSY) {
-            tma_box(zsa, &P.tm[0][7], x0c, by - 1, bz - 1, bar);
-            tma_box(ysa, &P.tm[1][7], x0c, by - 1, bz - 1, bar);
-            tma_box(xsa, &P.tm[2][7], x0c, by, bz - 1, bar);
-        }
+        tma_box(sb, &P.tm[0][0], x0, by - 1, bz - 1, bar);
+        tma_box(sb + R::OFF_Y, &P.tm[1][0], x0, by - 1, bz - 1, bar);
+        tma_box(sb + R::OFF_X, &P.tm[2][0], y0, bz - 1, bx - 1, bar);
+        tma_box(sb + R::OFF_ZC, &P.tm[0][1], x0c, by - 1, bz - 1, bar);
+        tma_box(sb + R::OFF_YC, &P.tm[1][1], x0c, by - 1, bz - 1, bar);
+        tma_box(sb + R::OFF_XC, &P.tm[2][1], x0c, by, bz - 1, bar);
+        ++s_niss[b];
     };
     // the tile column of this thread: registers row i <-> r = i-1
     float ex[NR], ey[NR], ez[NR], hx[NR], hy[NR], hz[NR];
@@ -266,6 +282,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
         if (tid == 0) {
             s_ticket = atomicAdd(P.ctrl, 1);
             s_abort = ld_volatile(P.ctrl + 1) != DEV_OK;
+            s_pref = 0;
         }
         if (tid < 3) s_seen[tid] = 0u;
         __syncthreads();
@@ -332,23 +349,38 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
         if (iv.s > 0 && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.s);
 
         bool abort = false;
-        bool pref = false;  // this step's shells were issued during the previous step
+        // may a point source lie in the box during this tile's steps?  (per
+        // axis, the box holds coordinate c at steps A - c .. A - c + n - 1)
+        bool tile_src = false;
+        for (int q = 0; q < P.src.n; ++q) {
+            const SrcDesc &s = P.src.s[q];
+            const int lo = max(max(iv.s, Ax - s.i), max(Ay - s.j, Az - s.k));
+            const int hi = min(min(iv.e, Ax - s.i + TX - 1), min(Ay - s.j + TY - 1, Az - s.k + TZ - 1));
+            tile_src |= lo <= hi;
+        }
         for (int t = iv.s; t <= iv.e; ++t) {
             const int bx = Ax - t, by = Ay - t, bz = Az - t;  // box low corner at step t
             const int cur = R::NBUF == 2 ? (t & 1) : 0;
             char *const sb = stg0 + (size_t)cur * R::STG_B;
-            T *const ZST = reinterpret_cast<T *>(sb), *const YST = ZST + 6 * R::ZB, *const XST = YST + 6 * R::YB;
-            float *const ZSC = reinterpret_cast<float *>(sb + R::FST_B), *const YSC = ZSC + R::ZBC;
-            float *const XSC = YSC + R::YBC, *const ZSA = XSC + R::XBC, *const YSA = ZSA + R::ZBC;
-            float *const XSA = YSA + R::YBC;
+            const T *const ZST = reinterpret_cast<const T *>(sb);
+            const T *const YST = reinterpret_cast<const T *>(sb + R::OFF_Y);
+            const T *const XST = reinterpret_cast<const T *>(sb + R::OFF_X);
+            const float *const ZSC = reinterpret_cast<const float *>(sb + R::OFF_ZC), *const ZSA = ZSC + R::ZBC;
+            const float *const YSC = reinterpret_cast<const float *>(sb + R::OFF_YC), *const YSA = YSC + R::YBC;
+            const float *const XSC = reinterpret_cast<const float *>(sb + R::OFF_XC), *const XSA = XSC + R::XBC;
             const int dx = (lane - bx) & 31, dy = (w - by) & (R::RY - 1);
             const int px = bx + dx, py = by + dy;
             const bool xbox = dx < TX, ybox = dy < TY;
             const bool colin = xbox && ybox && (unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny;
             const int ey_w = (by - 1) & (R::RY - 1);  // warp holding the y shell this step
+            const int yf_w = (by + TY) & (R::RY - 1);  // warp holding the top y row of step t-1
             const long long col = px + (long long)P.pitch * py;
             // rows i with physical z = bz + i - 1 inside the domain
             const int i_lo = max(1, 1 - bz), i_hi = min(NR, P.nz - bz + 1);
+            // the box lies inside the domain, clear of the low walls: every
+            // box cell is updated with no mask.  (The x-shell lane and the
+            // y-shell warp compute values that their refills overwrite.)
+            const bool inner = bx >= 1 && by >= 1 && bz >= 1 && bx + TX <= P.nx && by + TY <= P.ny && bz + TZ <= P.nz;
 
             // A. publish E^t (old) rows for the warp below's H half-step
 #pragma unroll
@@ -356,30 +388,34 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 XEx[(w * NZ + i) * 32 + lane] = ex[i];
                 XEz[(w * NZ + i) * 32 + lane] = ez[i];
             }
-            if (w == 0) {
-                const bool ok = wait_level(P, U, s_seen, t, ticket);
-                // may the next step's shells be fetched now?  (one poll)
-                const bool nxt = R::NBUF == 2 && ok && t + 1 <= iv.e && level_ready(P, U, s_seen, t + 1);
-                if (tid == 0) {
-                    s_abort = !ok;
-                    s_pref = nxt;
-                }
-            }
             __syncthreads();  // B1
             if (s_abort) { abort = true; break; }
-            const bool pref_next = s_pref != 0;
+            // unless the previous step found this step's shells published,
+            // wait here for the upwind tiles' level t; fetch the shells now
+            // unless they were fetched during the previous step
+            const int pst = s_pref;
+            if (pst == 0) {
+                if (w == 0) {
+                    const bool ok = wait_level(P, U, s_seen, t, ticket);
+                    if (tid == 0) s_abort = !ok;
+                }
+                __syncthreads();
+                if (s_abort) { abort = true; break; }
+            }
+            if (pst != 1 && tid == 0) issue_shells(t, cur, Ax, Ay, Az);
 
             // B. the warp whose y slot leaves the tile this step is idle during
             //    the H half-step: it stores last step's top y face, which its
             //    registers still hold; all threads store the staged top x face
-            if (w == ey_w && t > iv.s) {
+            if (w == yf_w && t > iv.s) {
                 const int pbx = bx + 1, pby = by + 1, pbz = bz + 1;  // box corner of step t-1
                 const int pdx = (lane - pbx) & 31;
                 const int qx = pbx + pdx, qy = pby + TY - 1;
                 if (pdx < TX && (unsigned)qx < (unsigned)P.nx && (unsigned)qy < (unsigned)P.ny) {
                     const long long c2 = qx + (long long)P.pitch * qy;
+                    // (the top row, i = NR - 1, went out with the top z face)
 #pragma unroll
-                    for (int i = 1; i < NR; ++i) {
+                    for (int i = 1; i < NR - 1; ++i) {
                         const int qz = pbz + i - 1;
                         if ((unsigned)qz < (unsigned)P.nz) {
                             const long long g = c2 + sxy * qz;
@@ -389,34 +425,33 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 }
             }
             if (t > iv.s) STORE_XFACE(bx + 1, by + 1, bz + 1);  // top x face of step t-1, staged in XO
-            // lower shells of level t (unless fetched during the previous step),
-            // and those of level t+1 into the other buffer when they are ready
+            // x / y starts of the staged boxes (rounded down to 16 bytes)
             const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1), y0 = by & ~(XA - 1);
-            if (tid == 0) {
-                if (!pref) issue_shells(t, cur, Ax, Ay, Az);
-                if (pref_next) issue_shells(t + 1, cur ^ 1, Ax, Ay, Az);
-            }
-            if (!pref) (cur ? n_iss1 : n_iss0) += 1;
-            if (pref_next) (cur ? n_iss0 : n_iss1) += 1;
 
             // C. H half-step, top-down in place: H[i] <- H[i-1] - dt curl_f(E[i-1], E[i], ...)
-            if (w != ey_w) {
+            if (ybox) {
                 const int wn = (w + 1) & (R::RY - 1);
                 const int src = (lane + 1) & 31;
+                auto h_pass = [&](auto masked) {
 #pragma unroll
-                for (int i = NR - 1; i >= 1; --i) {
-                    const float ez_xp = shfl_from(ez[i - 1], src);
-                    const float ey_xp = shfl_from(ey[i - 1], src);
-                    const float ez_yp = XEz[(wn * NZ + (i - 1)) * 32 + lane];
-                    const float ex_yp = XEx[(wn * NZ + (i - 1)) * 32 + lane];
-                    const float nhx = h_x(hx[i - 1], ez_yp, ez[i - 1], ey[i], ey[i - 1], ndt);
-                    const float nhy = h_y(hy[i - 1], ex[i], ex[i - 1], ez_xp, ez[i - 1], ndt);
-                    const float nhz = h_z(hz[i - 1], ey_xp, ey[i - 1], ex_yp, ex[i - 1], ndt);
-                    const bool upd = colin && i >= i_lo && i < i_hi;
-                    hx[i] = upd ? RND(nhx, 3) : hx[i - 1];
-                    hy[i] = upd ? RND(nhy, 4) : hy[i - 1];
-                    hz[i] = upd ? RND(nhz, 5) : hz[i - 1];
-                }
+                    for (int i = NR - 1; i >= 1; --i) {
+                        const float ez_xp = shfl_from(ez[i - 1], src);
+                        const float ey_xp = shfl_from(ey[i - 1], src);
+                        const float ez_yp = XEz[(wn * NZ + (i - 1)) * 32 + lane];
+                        const float ex_yp = XEx[(wn * NZ + (i - 1)) * 32 + lane];
+                        const float nhx = h_x(hx[i - 1], ez_yp, ez[i - 1], ey[i], ey[i - 1], ndt);
+                        const float nhy = h_y(hy[i - 1], ex[i], ex[i - 1], ez_xp, ez[i - 1], ndt);
+                        const float nhz = h_z(hz[i - 1], ey_xp, ey[i - 1], ex_yp, ex[i - 1], ndt);
+                        const bool upd = !decltype(masked)::value || (colin && i >= i_lo && i < i_hi);
+                        hx[i] = upd ? RND(nhx, 3) : hx[i - 1];
+                        hy[i] = upd ? RND(nhy, 4) : hy[i - 1];
+                        hz[i] = upd ? RND(nhz, 5) : hz[i - 1];
+                    }
+                };
+                if (inner)
+                    h_pass(std::false_type());
+                else
+                    h_pass(std::true_type());
             }
             // every thread waits on the staging barrier itself: its completion
             // makes the copied shells visible to that thread, so no block
@@ -426,7 +461,6 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 if (!wait_stage(P, &s_bar[cur], nw & 1u, ticket)) s_abort = 1;
                 ++nw;
             }
-            pref = pref_next;
 
             // D. refills from the staged shells, then publish new H rows for the
             //    warp above's E half-step
@@ -445,6 +479,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YSC[i * SWC + xlc];
                     if (R::LOSSY) CAs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YSA[i * SWC + xlc];
                 }
+            } else if (!ybox) {  // the previous top y row (two outside slots): kept
             } else if (xbox) {  // row -1 takes the lower z shell's H and coefficient
                 const int o = (dy + 1) * SW + (px - x0), oc = (dy + 1) * SWC + (px - x0c);
                 hx[0] = S::dec(ZST[3 * R::ZB + o], SC(3));
@@ -472,13 +507,26 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             }
             __syncthreads();  // B2
             if (s_abort) { abort = true; break; }
-            if (t > iv.s && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)t);  // level t-1 done
+            // the warps outside the box in y sit out the E half-step: the y
+            // shell's checks (one poll) whether the upwind tiles have published
+            // level t+1 and fetches those shells into the other buffer if so
+            // (two buffers); the one holding the previous top y row (the same
+            // warp when the box leaves one y slot) publishes level t-1
+            if (w == ey_w) {
+                const bool nxt = t + 1 <= iv.e && level_ready(P, U, s_seen, t + 1);
+                __syncwarp();  // orders lanes 1, 2's acquires before lane 0's copies
+                if (lane == 0) {
+                    if (R::NBUF == 2 && nxt) issue_shells(t + 1, cur ^ 1, Ax, Ay, Az);
+                    s_pref = nxt ? (R::NBUF == 2 ? 1 : 2) : 0;
+                }
+            }
+            if (w == yf_w && lane == 0 && t > iv.s) publish(P, tile, ticket, P.epoch + (unsigned)t);  // level t-1 done
 
             // does this thread own a point source this step?  (16-bit storage:
             // its E rows are rounded after the source is added, not before)
             const long long step = P.step0 + t;
             bool srcthr = false;
-            if (S::narrow) {
+            if (S::narrow && tile_src) {
                 for (int q = 0; q < P.src.n; ++q) {
                     const SrcDesc &s = P.src.s[q];
                     srcthr |= step < s.n_amp && s.i >= bx && s.i < bx + TX && s.j >= by && s.j < by + TY &&
@@ -486,12 +534,12 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 }
             }
 
-            if (w != ey_w) {
+            if (ybox) {
                 // F. E half-step, top-down in place: E[i] <- E[i-1] + ce curl_b(H[i], H[i-1], ...)
                 const int wm = (w - 1) & (R::RY - 1);
                 const int src = (lane - 1) & 31;
                 const bool ux = py > 0, uy = px > 0, uz = px > 0 && py > 0;
-                auto e_pass = [&](auto round) {
+                auto e_pass = [&](auto round, auto masked) {
 #pragma unroll
                     for (int i = NR - 1; i >= 1; --i) {
                         const float hz_xm = shfl_from(hz[i], src);
@@ -508,20 +556,28 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                             ney = RND(ney, 1);
                             nez = RND(nez, 2);
                         }
-                        const bool in = colin && i >= i_lo && i < i_hi;
-                        const bool kz = bz + i - 1 > 0;
-                        ex[i] = (in && ux && kz) ? nex : ex[i - 1];
-                        ey[i] = (in && uy && kz) ? ney : ey[i - 1];
-                        ez[i] = (in && uz) ? nez : ez[i - 1];
+                        if (decltype(masked)::value) {
+                            const bool in = colin && i >= i_lo && i < i_hi;
+                            const bool kz = bz + i - 1 > 0;
+                            ex[i] = (in && ux && kz) ? nex : ex[i - 1];
+                            ey[i] = (in && uy && kz) ? ney : ey[i - 1];
+                            ez[i] = (in && uz) ? nez : ez[i - 1];
+                        } else {
+                            ex[i] = nex;
+                            ey[i] = ney;
+                            ez[i] = nez;
+                        }
                     }
                 };
                 // 16-bit storage rounds each new E value here, except in the
                 // (rare) thread that adds a point source this step: it rounds
-                // after the source, below
-                if (S::narrow && !srcthr)
-                    e_pass(std::integral_constant<bool, true>());
+                // after the source, below (masked form)
+                if (S::narrow && srcthr)
+                    e_pass(std::false_type(), std::true_type());
+                else if (inner)
+                    e_pass(std::bool_constant<S::narrow>(), std::false_type());
                 else
-                    e_pass(std::integral_constant<bool, false>());
+                    e_pass(std::bool_constant<S::narrow>(), std::true_type());
                 if (xbox) {  // row -1 takes the lower z shell's E (level t)
                     const int o = (dy + 1) * SW + (px - x0);
                     ex[0] = S::dec(ZST[0 * R::ZB + o], SC(0));
@@ -539,7 +595,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             }
 
             // point sources inside the box: the owning thread adds them
-            for (int q = 0; q < P.src.n; ++q) {
+            for (int q = 0; tile_src && q < P.src.n; ++q) {
                 const SrcDesc &s = P.src.s[q];
                 if (step < s.n_amp && s.i >= bx && s.i < bx + TX && s.j >= by && s.j < by + TY &&
                     s.k >= bz && s.k < bz + TZ && lane == (s.i & 31) && w == (s.j & (R::RY - 1))) {
@@ -629,8 +685,8 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     // after an abort, bulk copies may still be writing into the staging
     // buffers: wait for them (bounded) before the CTA's shared memory goes
     if (tid == 0) {
-        while (n_wait0 < n_iss0 && wait_stage(P, &s_bar[0], n_wait0 & 1u, -1)) ++n_wait0;
-        while (n_wait1 < n_iss1 && wait_stage(P, &s_bar[1], n_wait1 & 1u, -1)) ++n_wait1;
+        while (n_wait0 < s_niss[0] && wait_stage(P, &s_bar[0], n_wait0 & 1u, -1)) ++n_wait0;
+        while (n_wait1 < s_niss[1] && wait_stage(P, &s_bar[1], n_wait1 & 1u, -1)) ++n_wait1;
     }
 }
 
@@ -651,32 +707,35 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 
 // 31 x 15 x 12 and 31 x 15 x 8 tiles, each for every kernel format; the
 // lossy (absorber) form for the 31 x 15 x 12 tile
+// the box leaves one y slot of the ring outside (TY = 15): as fast as two
+// outside slots (TY = 14) and updates more cells per step
+constexpr int REG_TY = 15;
 template <int NZ>
 struct RegShape {
     static constexpr bool HAS_LOSSY = NZ == 12;
     static cudaError_t configure(int fmt, bool lossy)
     {
         if (lossy) {
-            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S, true>>());
+            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S, true, REG_TY>>());
             return cudaErrorInvalidValue;
         }
-        DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S, false>>());
+        DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S, false, REG_TY>>());
     }
     static int per_sm(int fmt, bool lossy)
     {
         if (lossy) {
-            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, occ<RegTile<NZ, S, true>>());
+            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, occ<RegTile<NZ, S, true, REG_TY>>());
             return 0;
         }
-        DISPATCH_FORMAT(fmt, S, occ<RegTile<NZ, S, false>>());
+        DISPATCH_FORMAT(fmt, S, occ<RegTile<NZ, S, false, REG_TY>>());
     }
     static cudaError_t launch(const SysLaunch &p, int grid, cudaStream_t st, int fmt)
     {
         if (p.ca) {
-            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S, true>>(p, grid, st));
+            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S, true, REG_TY>>(p, grid, st));
             return cudaErrorInvalidValue;
         }
-        DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S, false>>(p, grid, st));
+        DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S, false, REG_TY>>(p, grid, st));
     }
     template <class R>
     static cudaError_t set()
@@ -708,7 +767,7 @@ using RegB = RegShape<8>;   // 31 x 15 x 8
 
 int systolic_reg_rows(int k) { return (k == 0 ? 12 : 8) + 1; }
 
-SysShape systolic_reg_shape(int k) { return SysShape{31, 15, k == 0 ? 12 : 8}; }
+SysShape systolic_reg_shape(int k) { return SysShape{31, REG_TY, k == 0 ? 12 : 8}; }
 
 cudaError_t systolic_reg_configure(int k, int fmt, bool lossy)
 {
