@@ -29,10 +29,10 @@
 // itself.
 //
 // The warp whose y slot is outside the box sits out both half-steps, so it
-// carries the tile's bookkeeping: after the second barrier it polls the
-// upwind tiles' progress once for level t+1 and, if they have published it,
-// fetches those shells into the second staging buffer, and it publishes the
-// tile's own level t-1.  Only when that poll failed (or on a tile's first
+// carries the tile's bookkeeping: after the second barrier it publishes the
+// tile's own level t-1, then polls the upwind tiles' progress once for level
+// t+1 and, if they have published it, fetches those shells into the second
+// staging buffer.  Only when that poll failed (or on a tile's first
 // step) does warp 0 wait for the upwind tiles at the start of the step, and
 // thread 0 fetch the shells then.
 //
@@ -507,11 +507,13 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             }
             __syncthreads();  // B2
             if (s_abort) { abort = true; break; }
-            // the warps outside the box in y sit out the E half-step: the y
-            // shell's checks (one poll) whether the upwind tiles have published
-            // level t+1 and fetches those shells into the other buffer if so
-            // (two buffers); the one holding the previous top y row (the same
-            // warp when the box leaves one y slot) publishes level t-1
+            // the warps outside the box in y sit out the E half-step: the one
+            // holding the previous top y row (the y shell's when the box leaves
+            // one y slot) publishes level t-1; the y shell's then checks (one
+            // poll) whether the upwind tiles have published level t+1 and
+            // fetches those shells into the other buffer if so (two buffers).
+            // (The release first: the poll after it is cheaper than before it.)
+            if (w == yf_w && lane == 0 && t > iv.s) publish(P, tile, ticket, P.epoch + (unsigned)t);  // level t-1 done
             if (w == ey_w) {
                 const bool nxt = t + 1 <= iv.e && level_ready(P, U, s_seen, t + 1);
                 __syncwarp();  // orders lanes 1, 2's acquires before lane 0's copies
@@ -520,7 +522,6 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     s_pref = nxt ? (R::NBUF == 2 ? 1 : 2) : 0;
                 }
             }
-            if (w == yf_w && lane == 0 && t > iv.s) publish(P, tile, ticket, P.epoch + (unsigned)t);  // level t-1 done
 
             // does this thread own a point source this step?  (16-bit storage:
             // its E rows are rounded after the source is added, not before)
