@@ -236,8 +236,8 @@ fdtd_status fdtd_debug_set(fdtd_handle h, int32_t kind, int64_t ticket, int64_t 
  * FDTD_ERR_INVALID_ARG for null pointers, n_steps < 0 or dt <= 0. */
 #define FDTD_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 
-/* Learned boundary network (the benchmark spec's learned absorbing boundary; the
- * paper has no counterpart): f(x) = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3,
+/* Learned boundary network (a learned absorbing boundary; the paper has no
+ * counterpart): f(x) = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3,
  * 324 -> 64 -> 64 -> 6, FP32.  Parameter vector, in this order: W1 [64][324],
  * b1 [64], W2 [64][64], b2 [64], W3 [6][64], b3 [6] (row = output unit).
  * Input x: x[(s*6 + c)*27 + (dz+1)*9 + (dy+1)*3 + (dx+1)] for the fields c =

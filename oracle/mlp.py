@@ -4,8 +4,8 @@ step.
 TEST INFRASTRUCTURE ONLY: imported by tests/ (and nothing in the product
 path).  Plain numpy, float64, written from the definitions:
 
-Network (the benchmark spec (4): 2 hidden layers of 64, input the 3x3x3 stencil of
-the 6 fields at steps n and n-1):
+Network (the learned absorbing boundary: 2 hidden layers of 64, input the
+3x3x3 stencil of the 6 fields at steps n and n-1):
     f(x) = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3,   x in R^324, f in R^6.
 Parameter vector (FP32 on the GPU), in this order:
     W1 [64][324], b1 [64], W2 [64][64], b2 [64], W3 [6][64], b3 [6]

@@ -3,8 +3,7 @@ library's kernels through the C ABI (fdtd_learned_record, fdtd_mlp_train,
 FDTD_BOUNDARY_LEARNED).  Orchestration only; every arithmetic step runs in
 libfdtd's CUDA kernels.
 
-Set-up (the benchmark spec (4)): the learned boundary replaces a thick graded
-absorber.  A reference domain is the learned domain D (n^3 cells, its outer
+Set-up: the learned boundary replaces a thick graded absorber.  A reference domain is the learned domain D (n^3 cells, its outer
 `thickness` cells a graded base layer) surrounded by `pad` more cells whose
 outer `absorber` cells conduct (graded, order 3); the network learns, for
 D's face cells, the correction from D's own Yee step (PEC walls) to the
@@ -15,8 +14,8 @@ alone with the learned layer at its walls.
 Reflection of a boundary: run the same source in D with that boundary and
 in the reference domain; the error is the energy of the difference in D's
 interior (cells not in the layer) summed over the run, relative to the
-reference's energy there.  The thick absorber is the judge (its own error
-is zero by definition); a plain PEC wall, a graded absorber as thin as the
+reference's energy there.  The thick absorber is the yardstick (its own
+error is zero by definition); a plain PEC wall, a graded absorber as thin as the
 learned layer, and the learned layer are compared on it.
 """
 import numpy as np
@@ -68,7 +67,7 @@ class Setup:
         return sig
 
     def ref_sim(self, scheme="systolic", max_source_steps=0, with_layer=True):
-        """The reference domain; with_layer=False is the judge: the thick
+        """The reference domain; with_layer=False is the yardstick: the thick
         absorber alone."""
         shape = (self.N,) * 3
         return fdtd.Sim(shape, self.eps_bg, DT, scheme=scheme, boundary="graded",

@@ -7,7 +7,7 @@
 * One learned-boundary run against the FP64 learned-boundary step.
 * The gain: trained on thick-absorber runs, the 4-cell learned layer
   reflects less than a PEC wall and than a graded absorber of the same
-  4 cells (judged against the thick absorber).
+  4 cells (measured against the thick absorber).
 """
 import numpy as np
 import pytest
@@ -139,7 +139,7 @@ def test_learned_layer_beats_pec_and_a_thin_absorber(cuda_device):
     # the 4-cell learned boundary (graded base, learned termination), trained
     # on pulses plus broadband initial noise (without the fine-grained
     # patterns the closed loop can meet patterns the network never saw and
-    # grow them), judged against the 32-cell absorber
+    # grow them), measured against the 32-cell absorber
     setup = learned.Setup(n=48, thickness=4, pad=32, absorber=(32, 0.5, 3), base_sigma=0.3)
     x, y = learned.record(setup, seed=1, runs=4, sources_per_run=3, steps=250, per_step=1000, noise=0.05)  # 10^6 pairs
     assert torch.isfinite(x).all() and torch.isfinite(y).all()
