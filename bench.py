@@ -47,6 +47,10 @@ DEFAULT_TILE = "31x15x12"
 # the launch's fixed initial load and final flush (52 B per cell) taken out;
 # None for kernels whose counters have not been taken since they changed.
 MEASURED_TRAFFIC = {"31x15x12": 11.33}
+# Warp instructions issued per cell update (smsp__inst_executed.sum over the
+# updates) in the same capture: with the bench's GCUPS it gives the SM
+# sub-partitions' issue rate, the resource this kernel runs against.
+MEASURED_WARP_INST = {"31x15x12": 3.956}
 
 
 STORAGE_BYTES = {"f32": 4, "f16": 2, "bf16": 2}
@@ -653,6 +657,16 @@ def main():
     per_update = MEASURED_TRAFFIC.get(tile) if args.scheme == "systolic" and args.storage == "f32" else None
     traffic = per_update * cell_steps_per_launch + 52.0 * cells if per_update else None
     achieved = sys_bytes * cell_steps_per_launch / per_launch_s / 1e9
+    # issue roofline: one warp instruction per clock per SM sub-partition
+    wi = MEASURED_WARP_INST.get(tile) if args.scheme == "systolic" and args.storage == "f32" else None
+    issue = None
+    if wi and clk and clk.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+        peak_i = sms * 4 * clk["sm_mhz"] * 1e6 / 1e12
+        ach_i = gcups / world * 1e9 * wi / 1e12
+        issue = {"warp_instructions_per_cell_update": wi, "achieved": ach_i, "peak": peak_i,
+                 "unit": "T warp instructions/s", "frac": ach_i / peak_i,
+                 "peak_from": f"{sms} SMs x 4 sub-partitions x 1 instruction/clock x sampled SM clock"}
     line = {
         "metric": "GCUPS of 3D Yee update, systolic vs naive kernel, FP32 & FP16-stored, 1 GB300",
         "value": gcups, "unit": "GCUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -667,6 +681,7 @@ def main():
                             "bound_gcups": peak / (12.0 * eb),
                             "frac": gcups / world / (peak / (12.0 * eb)), "peak_kind": peak_kind},
         "dram_gbs_measured": (per_update * cells * STEPS_PER_CALL * args.steps / elapsed / 1e9) if per_update else None,
+        "issue_roofline": issue,
         "paper_context": {"tcups_abstract": 0.15, "tcups_introduction": 0.18, "hardware": "1x H100",
                           "conditions": "16-bit fields, eps and sigma, no sources, domain size not stated",
                           "note": "context only, not this workload"},

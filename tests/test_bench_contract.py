@@ -37,3 +37,6 @@ def test_bench_line_has_the_contract_keys():
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] >= 1
     assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]
+    ir = d.get("issue_roofline")
+    if ir is not None:  # measured instruction count x GCUPS against the SMs' issue rate
+        assert 0 < ir["frac"] <= 1.0 and abs(ir["frac"] - ir["achieved"] / ir["peak"]) < 1e-9
