@@ -41,7 +41,10 @@
  *     thread-safe; different handles are independent.
  *   * Ownership: the caller allocates the device workspace (size from
  *     fdtd_workspace_size) and keeps it alive until fdtd_destroy; the library
- *     allocates nothing on the device.  Host-side state lives in the handle.
+ *     allocates nothing on the device.  Host-side state lives in the handle
+ *     (with the learned boundary also one internal CUDA stream and two
+ *     events, on which the network runs beside the Yee step; fdtd_destroy
+ *     releases them).
  */
 #ifndef FDTD_H
 #define FDTD_H
@@ -105,7 +108,10 @@ typedef struct {
  *     PEC walls get wrong: tangential E on a low face, tangential H on a
  *     high face.  A zero network leaves the graded layer on PEC walls.
  *     Naive scheme and FP32 storage only (the update needs the whole previous
- *     level every step, which the systolic tiles do not keep). */
+ *     level every step, which the systolic tiles do not keep).  Per step the
+ *     band of the state is snapshotted, the network runs on the handle's
+ *     internal stream while the Yee step runs on the handle's stream, and
+ *     the corrections are added once both are done. */
 typedef struct {
     int32_t kind;       /* FDTD_BOUNDARY_* */
     int32_t thickness;  /* absorber / learned layer thickness in cells, >= 1 */

@@ -30,9 +30,9 @@ struct Layout {
     size_t xface;      // register kernel's x-face buffer (6 components)
     long long xfs;     // its elements per component
     int nyp;           // its y extent padded to 16 bytes
-    // learned boundary: network, previous state, layer and band cell lists,
-    // layer predictions
-    size_t params, prev, layer, band, pred;
+    // learned boundary: network, previous and current band snapshots, layer
+    // and band cell lists, layer predictions
+    size_t params, prev, snap, layer, band, pred;
     long long nlayer, nband;
     int eb;     // bytes per stored field value (4 FP32, 2 FP16/BF16)
     int pitch;  // elements per x row in device memory (nx rounded up to 16 bytes)
@@ -111,13 +111,15 @@ bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, const fdtd_boundary &
     L.ca = off;  // E decay of conducting cells (absorber, or the learned layer's base)
     if (conducts(b)) off = align_up(off + sizeof(float) * (size_t)n);
     L.nlayer = L.nband = 0;
-    L.params = L.prev = L.layer = L.band = L.pred = off;
+    L.params = L.prev = L.snap = L.layer = L.band = L.pred = off;
     if (b.kind == FDTD_BOUNDARY_LEARNED) {
         L.nlayer = cells_within(g, 1);  // the faces carry the network's corrections
         L.nband = cells_within(g, 2);   // their stencils reach one cell further
         L.params = off;
         off = align_up(off + sizeof(float) * (size_t)mlpnet::NPARAM);
         L.prev = off;
+        off = align_up(off + 6 * align_up(sizeof(float) * (size_t)n));
+        L.snap = off;
         off = align_up(off + 6 * align_up(sizeof(float) * (size_t)n));
         L.layer = off;
         off = align_up(off + 3 * sizeof(int) * (size_t)L.nlayer);
@@ -400,6 +402,9 @@ struct fdtd_sim {
     float *ce;
     float *ca;     // E decay per cell (absorber), else null
     float *params, *prev, *pred;  // learned boundary (else null)
+    float *snap;                  // the band of the current state, read by the network
+    cudaStream_t aux;             // learned boundary: the network runs here, beside the Yee step
+    cudaEvent_t ev_fork, ev_join;
     int *layer, *band;
     int layer_grid;
     float *stage;  // dense FP32 component (16-bit storage), else null
@@ -523,6 +528,9 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     h->params = learned ? (float *)(h->ws + L.params) : nullptr;
     h->prev = learned ? (float *)(h->ws + L.prev) : nullptr;
     h->pred = learned ? (float *)(h->ws + L.pred) : nullptr;
+    h->snap = learned ? (float *)(h->ws + L.snap) : nullptr;
+    h->aux = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
     h->layer = learned ? (int *)(h->ws + L.layer) : nullptr;
     h->band = learned ? (int *)(h->ws + L.band) : nullptr;
     h->layer_grid = 0;
@@ -556,7 +564,7 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     h->eps_host.assign(eps, eps + n);
 
     auto fail = [&](fdtd_status st) {
-        delete h;
+        fdtd_destroy(h);
         return st;
     };
     // E coefficients, formed in FP64 and rounded to FP32 once per cell:
@@ -594,12 +602,19 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
         list_cells_within(*grid, 1, lcells);
         list_cells_within(*grid, 2, bcells);
         e = cudaMemcpyAsync(h->params, boundary->model, sizeof(float) * mlpnet::NPARAM, cudaMemcpyDefault, h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->prev, 0, L.layer - L.prev, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + L.prev, 0, L.layer - L.prev, h->stream);  // both snapshots
         if (e == cudaSuccess && !lcells.empty())
             e = cudaMemcpyAsync(h->layer, lcells.data(), sizeof(int) * lcells.size(), cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess && !bcells.empty())
             e = cudaMemcpyAsync(h->band, bcells.data(), sizeof(int) * bcells.size(), cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess) e = learned_layer_configure();
+        // the network's stream: highest priority, so its CTAs are placed first
+        // and the Yee kernels fill the rest of each SM
+        int lo = 0, hi = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
         int dev = 0, sms = 0;
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -687,7 +702,8 @@ fdtd_status fdtd_write_fields(fdtd_handle h, const float *src)
         }
     }
     CK(cudaMemsetAsync(h->ctrl + 1, 0, 3 * sizeof(int), h->stream));
-    if (h->prev) CK(cudaMemsetAsync(h->prev, 0, h->L.layer - h->L.prev, h->stream));  // S^{n-1} := 0
+    // S^{n-1} := 0 (both band snapshots: which is "previous" alternates)
+    if (h->prev) CK(cudaMemsetAsync(h->ws + h->L.prev, 0, h->L.layer - h->L.prev, h->stream));
     h->failed = false;
     return FDTD_OK;
 }
@@ -704,14 +720,23 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
             const long long fs = (long long)(h->L.fields[1] - h->L.fields[0]) / 4;
             const long long ps = (long long)align_up(sizeof(float) * (size_t)h->L.pitch * h->g.ny * h->g.nz) / 4;
             if (fs != ps) return FDTD_ERR_STATE;  // previous-state arrays mirror the field layout
+            // per step: snapshot the band of S^n; the network (S^n and S^{n-1}
+            // bands -> corrections) on the internal stream, the Yee step on the
+            // caller's, both at once; then the corrections are added and the
+            // snapshot becomes the next step's previous state
             for (int64_t s = 0; s < n; ++s) {
-                CK(learned_layer_predict(h->params, f0, h->prev, fs, h->L.pitch, h->g.nx, h->g.ny, h->g.nz,
-                                         h->layer, (int)h->L.nlayer, h->pred, h->layer_grid, h->stream));
-                CK(learned_copy_cells(h->prev, f0, fs, h->L.pitch, h->g.ny, h->band, (int)h->L.nband, h->stream));
+                CK(learned_copy_cells(h->snap, f0, fs, h->L.pitch, h->g.ny, h->band, (int)h->L.nband, h->stream));
+                CK(cudaEventRecord(h->ev_fork, h->stream));
+                CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+                CK(learned_layer_predict(h->params, h->snap, h->prev, fs, h->L.pitch, h->g.nx, h->g.ny, h->g.nz,
+                                         h->layer, (int)h->L.nlayer, h->pred, h->layer_grid, h->aux));
+                CK(cudaEventRecord(h->ev_join, h->aux));
                 CK(launch_naive_h(h->f, h->fmt, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, ndt, h->sc, h->stream));
                 CK(launch_naive_e(h->f, h->fmt, h->ce, h->ca, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, h->step, h->src,
                                   h->sc, h->stream));
+                CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
                 CK(learned_layer_scatter(f0, fs, h->L.pitch, h->g.ny, h->layer, (int)h->L.nlayer, h->pred, h->stream));
+                std::swap(h->prev, h->snap);
                 h->launches += 5;
                 h->step += 1;
             }
@@ -849,7 +874,17 @@ const char *fdtd_status_string(fdtd_status s)
     return "unknown status";
 }
 
-void fdtd_destroy(fdtd_handle h) { delete h; }
+void fdtd_destroy(fdtd_handle h)
+{
+    if (!h) return;
+    if (h->aux) {
+        cudaStreamSynchronize(h->aux);
+        cudaStreamDestroy(h->aux);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    delete h;
+}
 
 // ------------------------------------------------ learned-boundary network
 
