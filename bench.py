@@ -42,15 +42,17 @@ TILE_SHAPES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15), "31x15x12": (31
 DEFAULT_TILE = "31x15x12"
 
 
-# DRAM bytes per cell update measured with ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on a 100-step, 256^3 capture of the same kernel, with
-# the launch's fixed initial load and final flush (52 B per cell) taken out;
-# None for kernels whose counters have not been taken since they changed.
-MEASURED_TRAFFIC = {"31x15x12": 11.33}
+# DRAM bytes per cell update from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of a 100-step, 256^3 launch of the same kernel, with
+# the launch's fixed initial load and final flush (52 B per cell) taken out.
+# This run does not measure them: the line scales them by its own cell
+# updates and labels them as taken from the capture.  A kernel changed since
+# its capture has no entry (its traffic is then reported as null).
+CAPTURED_TRAFFIC = {"31x15x12": 11.33}
 # Warp instructions issued per cell update (smsp__inst_executed.sum over the
 # updates) in the same capture: with the bench's GCUPS it gives the SM
 # sub-partitions' issue rate, the resource this kernel runs against.
-MEASURED_WARP_INST = {"31x15x12": 3.956}
+CAPTURED_WARP_INST = {"31x15x12": 3.956}
 
 
 STORAGE_BYTES = {"f32": 4, "f16": 2, "bf16": 2}
@@ -135,28 +137,64 @@ def make_workload(shape):
     return eps, J, src
 
 
-def cpu_baseline(shape, budget_s=15.0):
-    """The FP64 oracle as it stands, on this host's cores, on a bounded
-    sample of the workload: the same grid and geometry for as many steps as
-    fit in ~budget_s (at least 1)."""
+def cpu_model():
+    """The host CPU's model string (from /proc/cpuinfo; Arm hosts give no
+    'model name', so their implementer / part codes are reported)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    for key in ("model name", "Model", "Hardware"):
+        for ln in lines:
+            if ln.split(":")[0].strip() == key:
+                return ln.split(":", 1)[1].strip()
+    impl = [ln.split(":", 1)[1].strip() for ln in lines if ln.startswith("CPU implementer")]
+    part = [ln.split(":", 1)[1].strip() for ln in lines if ln.startswith("CPU part")]
+    if impl and part:
+        return f"CPU implementer {impl[0]}, part {part[0]}"
+    return None
+
+
+def _oracle_rate(shape, threads, budget_s):
+    """Cell updates per second (in G) of the FP64 oracle with `threads` host
+    threads on the bench workload's grid, geometry and source, for as many
+    steps as fit in ~budget_s (at least 1); returns (gcups, steps, seconds)."""
     from oracle import YeeOracle
+    from oracle.yee import set_threads
     from paper_2502_20610_gb300 import workloads as wl
+    used = set_threads(threads)
     eps, J, (c, i, j, k) = make_workload(shape)
     o = YeeOracle(shape, wl.DT_DEFAULT, eps)
     o.add_source(c, i, j, k, J)
     o.step(1)  # first touch of the arrays
     t0 = time.perf_counter()
-    o.step(2)
-    t1 = (time.perf_counter() - t0) / 2
+    o.step(1)
+    t1 = time.perf_counter() - t0
     n = max(1, min(STEPS_PER_CALL, int(budget_s / max(t1, 1e-6))))
     t0 = time.perf_counter()
     o.step(n)
     dt = time.perf_counter() - t0
+    o.close()
     cells = shape[0] * shape[1] * shape[2]
+    return cells * n / dt / 1e9, n, dt, used
+
+
+def cpu_baseline(shape, budget_s=15.0, budget_1t_s=10.0):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded
+    sample of the workload: the same grid and geometry for as many steps as
+    fit in ~budget_s, with every core the process may use; and the same with
+    one thread."""
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": cells * n / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+    v, n, dt, used = _oracle_rate(shape, cores, budget_s)
+    v1, n1, dt1, _ = _oracle_rate(shape, 1, budget_1t_s)
+    from oracle.yee import set_threads
+    set_threads(cores)
+    return {"value": v, "unit": "GCUPS", "cores": used, "kind": "oracle",
             "sample": f"{shape[2]}x{shape[1]}x{shape[0]} grid, same eps map and source, {n} steps "
-                      f"(of {STEPS_PER_CALL}), FP64, {dt:.1f} s"}
+                      f"(of {STEPS_PER_CALL}), FP64, {dt:.1f} s",
+            "value_1_thread": v1, "sample_1_thread": f"{n1} steps, {dt1:.1f} s",
+            "cpu_model": cpu_model()}
 
 
 def dist_setup():
@@ -193,8 +231,11 @@ def run_reference(args, world, rank):
     if rank != 0:
         return 0
     from oracle import YeeOracle
+    from oracle.yee import set_threads
     from paper_2502_20610_gb300 import workloads as wl
     shape = GRID
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = set_threads(cores)
     eps, J, (c, i, j, k) = make_workload(shape)
     o = YeeOracle(shape, wl.DT_DEFAULT, eps)
     o.add_source(c, i, j, k, J)
@@ -212,9 +253,9 @@ def run_reference(args, world, rank):
     el = time.perf_counter() - t0
     cells = shape[0] * shape[1] * shape[2]
     v = cells * n * args.steps / el / 1e9
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     cb = {"value": v, "unit": "GCUPS", "cores": cores, "kind": "oracle",
-          "sample": f"each step: {n} oracle steps (of {STEPS_PER_CALL}) of the same workload, FP64"}
+          "sample": f"each step: {n} oracle steps (of {STEPS_PER_CALL}) of the same workload, FP64",
+          "cpu_model": cpu_model()}
     line = {"impl": "reference", "metric": "GCUPS of 3D Yee update, systolic vs naive kernel, FP32 & FP16-stored, 1 GB300",
             "value": v, "unit": "GCUPS", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
@@ -654,17 +695,18 @@ def main():
     tile = args.tile or DEFAULT_TILE
     eb = STORAGE_BYTES[args.storage]
     sys_bytes = systolic_bytes(tile, eb) if args.scheme == "systolic" else naive_bytes(eb)
-    per_update = MEASURED_TRAFFIC.get(tile) if args.scheme == "systolic" and args.storage == "f32" else None
+    per_update = CAPTURED_TRAFFIC.get(tile) if args.scheme == "systolic" and args.storage == "f32" else None
     traffic = per_update * cell_steps_per_launch + 52.0 * cells if per_update else None
     achieved = sys_bytes * cell_steps_per_launch / per_launch_s / 1e9
     # issue roofline: one warp instruction per clock per SM sub-partition
-    wi = MEASURED_WARP_INST.get(tile) if args.scheme == "systolic" and args.storage == "f32" else None
+    wi = CAPTURED_WARP_INST.get(tile) if args.scheme == "systolic" and args.storage == "f32" else None
     issue = None
     if wi and clk and clk.get("sm_mhz"):
         sms = torch.cuda.get_device_properties(device).multi_processor_count
         peak_i = sms * 4 * clk["sm_mhz"] * 1e6 / 1e12
         ach_i = gcups / world * 1e9 * wi / 1e12
-        issue = {"warp_instructions_per_cell_update": wi, "achieved": ach_i, "peak": peak_i,
+        issue = {"warp_instructions_per_cell_update": wi, "warp_instructions_source": "ncu capture (256^3, 100 steps)",
+                 "achieved": ach_i, "peak": peak_i,
                  "unit": "T warp instructions/s", "frac": ach_i / peak_i,
                  "peak_from": f"{sms} SMs x 4 sub-partitions x 1 instruction/clock x sampled SM clock"}
     line = {
@@ -675,12 +717,14 @@ def main():
         "scheme": args.scheme, "storage": args.storage,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "traffic_source": ("ncu capture of the same kernel (256^3, 100 steps), bytes per update "
+                                        "scaled to this launch" if traffic else None),
                      "kernel": "systolic_reg_kernel" if args.scheme == "systolic" else "naive_h/e",
                      "tile": tile, "algorithmic_bytes_per_cell_step": round(sys_bytes, 3)},
         "stream_roofline": {"bytes_per_cell_step": 12.0 * eb,
                             "bound_gcups": peak / (12.0 * eb),
                             "frac": gcups / world / (peak / (12.0 * eb)), "peak_kind": peak_kind},
-        "dram_gbs_measured": (per_update * cells * STEPS_PER_CALL * args.steps / elapsed / 1e9) if per_update else None,
+        "dram_gbs_from_capture": (per_update * cells * STEPS_PER_CALL * args.steps / elapsed / 1e9) if per_update else None,
         "issue_roofline": issue,
         "paper_context": {"tcups_abstract": 0.15, "tcups_introduction": 0.18, "hardware": "1x H100",
                           "conditions": "16-bit fields, eps and sigma, no sources, domain size not stated",

@@ -239,7 +239,8 @@ fdtd_status fdtd_debug_set(fdtd_handle h, int32_t kind, int64_t ticket, int64_t 
  * overlap on the GPU (two streams, two threads) race: serialise them.
  * The call is synchronous: it returns after the steps finish, with
  * FDTD_ERR_TIMEOUT if a device wait ran out, FDTD_ERR_CUDA on a CUDA error,
- * FDTD_ERR_INVALID_ARG for null pointers, n_steps < 0 or dt <= 0. */
+ * FDTD_ERR_INVALID_ARG for null pointers, an extent above 2^20, n_steps < 0
+ * or a dt that is not a finite positive number. */
 #define FDTD_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 
 /* Learned boundary network (a learned absorbing boundary; the paper has no

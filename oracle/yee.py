@@ -52,12 +52,20 @@ def _load():
     lib.oracle_set_eps_sigma.argtypes = [P, D, D, ctypes.c_int]
     lib.oracle_graded_sigma.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, ctypes.c_int, D]
     lib.oracle_get_ca.argtypes = [P, D]
+    lib.oracle_set_threads.restype = ctypes.c_int
+    lib.oracle_set_threads.argtypes = [ctypes.c_int]
     _lib = lib
     return lib
 
 
 #: 16-bit storage formats: (significant bits p, emin, emax)
 FORMATS = {"f16": (11, -14, 15), "bf16": (8, -126, 127)}
+
+
+def set_threads(n):
+    """Host threads of the oracle's parallel loops from now on (timing only;
+    results do not depend on it).  Returns the count in effect."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def round_to_format(x, fmt):

@@ -52,6 +52,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_MAX_SOURCES 16
 
@@ -304,6 +307,21 @@ static void half_step_e(yee_oracle *o, double **eout)
 }
 
 /* Advance n full steps: (E^m, H^{m-1/2}) -> (E^{m+n}, H^{m+n-1/2}). */
+/* Threads the parallel loops use from now on (n >= 1); returns the number
+ * in effect (1 when built without OpenMP).  Timing only: the results do not
+ * depend on it (every loop writes disjoint cells; the energy reduction is
+ * not used by the stepper). */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 int oracle_step(yee_oracle *o, long n)
 {
     long nc = ncell(o);

@@ -7,6 +7,7 @@
 #include "internal.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 #include <vector>
@@ -70,7 +71,8 @@ long long tiles_for(const fdtd_grid &g, int T)
 {
     const SysShape sh = systolic_shape(NOALLOC_VARIANT);
     auto cd = [](long long a, long long b) { return (a + b - 1) / b; };
-    return cd(g.nx + T - 1, sh.tx) * cd(g.ny + T - 1, sh.ty) * cd(g.nz + T - 1, sh.tz);
+    return cd((long long)g.nx + T - 1, sh.tx) * cd((long long)g.ny + T - 1, sh.ty) *
+           cd((long long)g.nz + T - 1, sh.tz);
 }
 
 } // namespace
@@ -78,8 +80,11 @@ long long tiles_for(const fdtd_grid &g, int T)
 extern "C" fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *d_fields, const float *d_coef,
                                                   double dt, int64_t n_steps, void *stream)
 {
-    if (!grid || !d_fields || !d_coef || n_steps < 0 || !(dt > 0.0)) return FDTD_ERR_INVALID_ARG;
+    if (!grid || !d_fields || !d_coef || n_steps < 0 || !(dt > 0.0) || !std::isfinite(dt))
+        return FDTD_ERR_INVALID_ARG;
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return FDTD_ERR_INVALID_ARG;
+    // the same extent limit as fdtd_create
+    if (grid->nx > (1 << 20) || grid->ny > (1 << 20) || grid->nz > (1 << 20)) return FDTD_ERR_INVALID_ARG;
     if (n_steps == 0) return FDTD_OK;
     const fdtd_grid g = *grid;
     // largest steps-per-launch whose tile grid fits the scratch array

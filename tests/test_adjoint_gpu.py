@@ -27,12 +27,23 @@ def small_problem(scheme="systolic", K=20, steps=80):
 
 
 def oracle_grad(p, eps_box):
+    # the GPU steps with c = fl32(dt/eps); the oracle takes the same
+    # coefficients (quantize=True), so what remains is FP32 arithmetic
     obj = adj.Objective(p.k0, p.mode.numpy().astype(np.float64), p.window)
     c, i, j, k, J = p.source
     f0 = np.zeros((6,) + p.shape)
-    L, g = adj.gradient(p.shape, p.eps_with(eps_box), f0, p.n_steps, [(c, i, j, k, J)], obj, DT)
+    L, g = adj.gradient(p.shape, p.eps_with(eps_box), f0, p.n_steps, [(c, i, j, k, J)], obj, DT, quantize=True)
     (x0, y0, z0), (x1, y1, z1) = p.box_lo, p.box_hi
     return L, g[z0:z1, y0:y1, x0:x1]
+
+
+# FP32 bound of the gradient: forward state and adjoint state each carry a
+# rounding error that grows at most linearly in the steps (the Yee map and
+# its transpose do not amplify: energy-norm stable), u32 = 2^-24 per
+# operation, ~10 operations per value and step, so after N = 80 steps each
+# is within ~N * 10 * u32 = 4.8e-5 of its FP64 value relative to its size,
+# and the gradient (their products summed in FP64) within ~1e-4 of it.
+GRAD_TOL = 1e-4
 
 
 @pytest.mark.parametrize("scheme,K", [("systolic", 20), ("naive", 7), ("systolic", 80)])
@@ -41,8 +52,10 @@ def test_gradient_matches_oracle_adjoint(cuda_device, scheme, K):
     L, g = p.run(eps_box)
     Lo, go = oracle_grad(p, eps_box)
     g = g.cpu().numpy()
+    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
+    print(f"{scheme} K={K}: |L-Lo|/Lo = {abs(L - Lo) / Lo:.2e}, gradient rel-L2 = {rel:.2e}")
     assert abs(L - Lo) <= 1e-4 * Lo
-    assert np.linalg.norm(g - go) <= 2e-3 * np.linalg.norm(go), np.linalg.norm(g - go) / np.linalg.norm(go)
+    assert rel <= GRAD_TOL, rel
 
 
 def test_gradient_is_independent_of_checkpoint_interval(cuda_device):
@@ -61,18 +74,26 @@ def test_autograd_and_finite_differences(cuda_device):
     (g,) = torch.autograd.grad(3.0 * L, x)
     _, g_direct = p.run(eps_box)
     assert torch.allclose(g, 3.0 * g_direct.cpu(), rtol=0, atol=0)
-    # central differences of the FP64 oracle on voxels of the box
+    # central differences of the FP64 oracle on 16 seeded random voxels of
+    # the box (distinct, drawn from the splitmix64 stream of the inputs)
     obj = adj.Objective(p.k0, p.mode.numpy().astype(np.float64), p.window)
     c, i, j, k, J = p.source
     f0 = np.zeros((6,) + p.shape)
-    rng = np.random.default_rng(5)
-    for _ in range(4):
-        q = tuple(int(rng.integers(0, s)) for s in eps_box.shape)
-        h = 1e-4 * eps_box[q]
+    n_box = eps_box.size
+    order = np.argsort(wl.splitmix64(17, 0, n_box))
+    voxels = [np.unravel_index(int(v), eps_box.shape) for v in order[:16]]
+    assert len(set(voxels)) == 16
+    worst = 0.0
+    for q in voxels:
+        q = tuple(int(v) for v in q)
+        h = 1e-5 * eps_box[q]  # truncation error ~(h/eps)^2 stays far below the tolerance
         ep, em = eps_box.copy(), eps_box.copy()
         ep[q] += h
         em[q] -= h
         fd = (adj.objective(p.shape, p.eps_with(ep), f0, p.n_steps, [(c, i, j, k, J)], obj, DT) -
               adj.objective(p.shape, p.eps_with(em), f0, p.n_steps, [(c, i, j, k, J)], obj, DT)) / (2 * h)
         got = float(g_direct[q])
-        assert abs(got - fd) <= 5e-3 * max(abs(fd), 1e-2 * float(g_direct.abs().max())), (q, got, fd)
+        scale = max(abs(fd), 1e-2 * float(g_direct.abs().max()))
+        worst = max(worst, abs(got - fd) / scale)
+        assert abs(got - fd) <= 1e-3 * scale, (q, got, fd)
+    print(f"16 voxels: largest |adjoint - central difference| / scale = {worst:.2e}")
