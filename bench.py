@@ -48,11 +48,11 @@ DEFAULT_TILE = "31x15x12"
 # This run does not measure them: the line scales them by its own cell
 # updates and labels them as taken from the capture.  A kernel changed since
 # its capture has no entry (its traffic is then reported as null).
-CAPTURED_TRAFFIC = {"31x15x12": 11.33}
+CAPTURED_TRAFFIC = {"31x15x12": 10.72}
 # Warp instructions issued per cell update (smsp__inst_executed.sum over the
 # updates) in the same capture: with the bench's GCUPS it gives the SM
 # sub-partitions' issue rate, the resource this kernel runs against.
-CAPTURED_WARP_INST = {"31x15x12": 3.956}
+CAPTURED_WARP_INST = {"31x15x12": 3.77}
 
 
 STORAGE_BYTES = {"f32": 4, "f16": 2, "bf16": 2}
@@ -385,6 +385,8 @@ def run_sweep(args):
         return run_config4(device, stream, measure)
     if args.sweep == "config5":
         return run_config5(device)
+    if args.sweep == "errors":
+        return run_errors(device)
     # sizes: the Si/SiO2 workload at 128^3 .. 1024^3, three storage formats
     steps = args.steps_per_call if args.steps_per_call != STEPS_PER_CALL else 1000
     for n in (128, 256, 512, 768, 1024):
@@ -402,6 +404,67 @@ def run_sweep(args):
                                   "stream_bound_gcups": load_peaks()[0] / (12.0 * eb),
                                   "stream_frac": g / (load_peaks()[0] / (12.0 * eb))}), flush=True)
             torch.cuda.empty_cache()
+    return 0
+
+
+def run_errors(device, sizes=(128, 256), steps=1000):
+    """Per-field relative L2 error against the FP64 oracle of the size
+    sweep's workload (Si/SiO2 seed 1, Jz dipole at the centre, 1000 steps) at
+    the sizes the oracle can follow: the systolic schedule with FP32, FP16 and
+    BF16 field storage, and beside each 16-bit format the error of the
+    oracle's own emulation of that storage rounding (FP64 arithmetic, the
+    same rounding points)."""
+    from oracle import YeeOracle
+    from oracle.yee import set_threads
+    from paper_2502_20610_gb300 import fdtd
+    from paper_2502_20610_gb300 import workloads as wl
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    set_threads(cores)
+    names = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")
+
+    def rel(got, ref):
+        total = np.sqrt((ref ** 2).sum())
+        out = {}
+        for c in range(6):
+            nb = np.sqrt((ref[c] ** 2).sum())
+            out[names[c]] = float(np.sqrt(((got[c] - ref[c]) ** 2).sum()) / (nb if nb >= 1e-6 * total else total))
+        return out
+
+    def oracle(shape, eps, src, storage, quantize):
+        o = YeeOracle(shape, wl.DT_DEFAULT, eps, quantize_ce_f32=quantize)
+        o.set_fields(np.zeros((6,) + shape))
+        if storage is not None:
+            o.set_storage(storage, [1.0] * 6)
+        o.add_source(*src)
+        o.step(steps)
+        f = o.fields()
+        o.close()
+        return f
+
+    for n in sizes:
+        shape = (n, n, n)
+        eps = wl.si_sio2_eps(shape, 1)
+        src = (2, n // 2, n // 2, n // 2, wl.sine_source(steps, wl.DT_DEFAULT, WAVELENGTH))
+        t0 = time.perf_counter()
+        ref = oracle(shape, eps, src, None, False)
+        t_or = time.perf_counter() - t0
+        refq = oracle(shape, eps, src, None, True)
+        for storage in ("f32", "f16", "bf16"):
+            sim = fdtd.Sim(shape, eps, wl.DT_DEFAULT, scheme="systolic", device=device, storage=storage,
+                           steps_per_launch=steps, max_source_steps=steps)
+            sim.add_source(*src)
+            sim.step(steps)
+            got = sim.read_fields().cpu().numpy().astype(np.float64)
+            sim.close()
+            row = {"sweep": "errors", "grid": n, "steps": steps, "storage": storage, "scheme": "systolic",
+                   "rel_l2_vs_fp64": rel(got, ref), "oracle_seconds": t_or, "oracle_threads": cores}
+            if storage == "f32":
+                row["rel_l2_vs_fp64_fp32_coefficients"] = rel(got, refq)
+            else:
+                row["emulation_rel_l2_vs_fp64"] = rel(oracle(shape, eps, src, storage, True), ref)
+            print(json.dumps(row), flush=True)
+            del got
+        del ref, refq
     return 0
 
 
@@ -571,7 +634,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"], help="field storage format")
     ap.add_argument("--no-16bit", action="store_true", help="skip the FP16/BF16 storage context lines")
     ap.add_argument("--no-1024", action="store_true", help="skip the 1024^3 context measurement")
-    ap.add_argument("--sweep", default=None, choices=["fig1", "sizes", "config4", "config5"],
+    ap.add_argument("--sweep", default=None, choices=["fig1", "sizes", "errors", "config4", "config5"],
                     help="print size-sweep lines instead of the benchmark line")
     ap.add_argument("--sweep-max-log2", type=int, default=28, help="fig1: largest grid, log2 of cells")
     args = ap.parse_args()

@@ -27,9 +27,9 @@ size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
     size_t fields[6], ce, ca, stage, src, progress, tiles, ctrl, total;
-    size_t xface;      // register kernel's x-face buffer (6 components)
-    long long xfs;     // its elements per component
-    int nyp;           // its y extent padded to 16 bytes
+    size_t xface, yface;  // register kernel's x- and y-face buffers (6 components each)
+    long long fxs, fys;   // their elements per component
+    int nzb, nzblk;       // their z extent: nzblk z-blocks of nzb / nzblk elements
     // learned boundary: network, previous and current band snapshots, layer
     // and band cell lists, layer predictions
     size_t params, prev, snap, layer, band, pred;
@@ -130,14 +130,23 @@ bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, const fdtd_boundary &
     }
     L.stage = off;
     if (c.storage != FDTD_STORAGE_F32) off = align_up(off + sizeof(float) * (size_t)g.nx * g.ny * g.nz);
-    L.nyp = (g.ny + q - 1) / q * q;
-    L.xfs = 0;
-    L.xface = off;
+    // face buffers of the register kernel: per component nx * ny columns of
+    // nzblk z-blocks (skewed z modulo nzblk * tile z, which the trail of
+    // faces never needs to span twice: see the kernel)
+    L.fxs = L.fys = 0;
+    L.nzb = L.nzblk = 0;
+    L.xface = L.yface = off;
     if (c.scheme == FDTD_SCHEME_SYSTOLIC && pick_variant(c) >= 2) {
-        const size_t per = align_up((size_t)L.eb * (size_t)g.nx * g.nz * L.nyp);
-        L.xfs = (long long)(per / L.eb);
+        const int tz = systolic_shape(pick_variant(c)).tz;
+        L.nzblk = ceil_div(g.nz, tz);
+        L.nzb = L.nzblk * face_block(tz, L.eb);
+        const size_t per = align_up((size_t)L.eb * (size_t)g.nx * g.ny * (size_t)L.nzb);
+        L.fxs = L.fys = (long long)(per / L.eb);
+        off += 6 * per;
+        L.yface = off;
         off += 6 * per;
     }
+    (void)q;
     L.source_steps = c.max_source_steps > 0 ? c.max_source_steps : DEFAULT_SOURCE_STEPS;
     L.src = off;
     off = align_up(off + sizeof(float) * (size_t)FDTD_MAX_SOURCES * (size_t)L.source_steps);
@@ -317,7 +326,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 }
 
 bool encode_shell_maps(CUtensorMap tm[3][2], void *fbase, long long fstride, const float *ce, const float *ca,
-                       int storage, int nx, int ny, int nz, int pitch, int nr, void *xf, long long xfs, int nyp)
+                       int storage, int nx, int ny, int nz, int pitch, int nr, int bz, void *xf, long long fxs,
+                       void *yf, long long fys, int nzb)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || fstride <= 0) return false;
@@ -328,6 +338,12 @@ bool encode_shell_maps(CUtensorMap tm[3][2], void *fbase, long long fstride, con
     const long long cstride_b = ca ? (long long)((const char *)ca - (const char *)ce) : 4 * n;
     if (cstride_b <= 0 || cstride_b % 16 != 0) return false;
     const cuuint64_t ncoef = ca ? 2 : 1;
+    auto map = [&](CUtensorMap *m, CUtensorMapDataType dt, void *base, const cuuint64_t dims[4],
+                   const cuuint64_t strides[3], const cuuint32_t box[4]) {
+        return enc(m, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
     for (int a = 0; a < 2; ++a) {
         const int eb = a == 0 ? storage_bytes(storage) : 4;
         const cuuint32_t xa = 16u / (cuuint32_t)eb, sw = 32u + xa;
@@ -338,31 +354,37 @@ bool encode_shell_maps(CUtensorMap tm[3][2], void *fbase, long long fstride, con
         const cuuint64_t strides[3] = {(cuuint64_t)pitch * eb, (cuuint64_t)pitch * (cuuint64_t)ny * eb,
                                        a == 0 ? (cuuint64_t)fstride * eb : (cuuint64_t)cstride_b};
         void *base = a == 0 ? fbase : (void *)ce;
-        // lower z shell {sw,16,1}, lower y shell {sw,1,nr} of every array
-        const cuuint32_t box[2][4] = {{sw, 16, 1, bf}, {sw, 1, (cuuint32_t)nr, bf}};
-        for (int s = 0; s < 2; ++s) {
-            if (enc(&tm[s][a], dt, 4, base, dims, strides, box[s], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                return false;
-        }
-        CUresult r;
+        // lower z shell {sw,16,1} of every array (fields and coefficients)
+        const cuuint32_t zbox[4] = {sw, 16, 1, bf};
+        if (!map(&tm[0][a], dt, base, dims, strides, zbox)) return false;
         if (a == 0) {
-            // lower x shell of the fields: from the x-face buffer, y innermost:
-            // dims {ny, nz, nx, 6}, box {16 + xa, nr, 1, 6}
-            const cuuint64_t xd[4] = {(cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nx, 6};
-            const cuuint64_t xs[3] = {(cuuint64_t)nyp * eb, (cuuint64_t)nyp * (cuuint64_t)nz * eb,
-                                      (cuuint64_t)xfs * eb};
-            const cuuint32_t xb[4] = {16u + xa, (cuuint32_t)nr, 1u, 6u};
-            r = enc(&tm[2][0], dt, 4, xf, xd, xs, xb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            // lower y and x shells of the fields from the face buffers, 5D maps
+            // {bz rows, columns along the face, the other axis, nzblk blocks,
+            // 6 fields}: y shell box {bz, 32, 1, 1, 6} (32 columns along x),
+            // x shell box {bz, 16, 1, 1, 6} (16 columns along y)
+            const cuuint64_t nzblk = (cuuint64_t)(nzb / bz);
+            const cuuint64_t ebz = (cuuint64_t)bz * eb;
+            const cuuint64_t yd[5] = {(cuuint64_t)bz, (cuuint64_t)nx, (cuuint64_t)ny, nzblk, 6};
+            const cuuint64_t ys[4] = {ebz, ebz * nx, ebz * nx * ny, (cuuint64_t)fys * eb};
+            const cuuint32_t yb[5] = {(cuuint32_t)bz, 32u, 1u, 1u, 6u};
+            const cuuint64_t xd[5] = {(cuuint64_t)bz, (cuuint64_t)ny, (cuuint64_t)nx, nzblk, 6};
+            const cuuint64_t xs[4] = {ebz, ebz * ny, ebz * nx * ny, (cuuint64_t)fxs * eb};
+            const cuuint32_t xb[5] = {(cuuint32_t)bz, 16u, 1u, 1u, 6u};
+            const cuuint32_t estr5[5] = {1, 1, 1, 1, 1};
+            if (enc(&tm[1][0], dt, 5, yf, yd, ys, yb, estr5, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
+            if (enc(&tm[2][0], dt, 5, xf, xd, xs, xb, estr5, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
         } else {
-            // lower x shell of the coefficients: a 16-byte x chunk {4,16,nr}
+            // lower y shell {sw,1,nr} and x shell (a 16-byte x chunk {4,16,nr})
+            // of the coefficients
+            const cuuint32_t ybox[4] = {sw, 1, (cuuint32_t)nr, bf};
+            if (!map(&tm[1][1], dt, base, dims, strides, ybox)) return false;
             const cuuint32_t xb[4] = {4u, 16u, (cuuint32_t)nr, bf};
-            r = enc(&tm[2][1], dt, 4, base, dims, strides, xb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (!map(&tm[2][1], dt, base, dims, strides, xb)) return false;
         }
-        if (r != CUDA_SUCCESS) return false;
     }
     return true;
 }
@@ -637,9 +659,10 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
         h->max_ctas = sms * per_sm;
         if (L.variant >= 2) {
             const long long fstride = (long long)(L.fields[1] - L.fields[0]) / L.eb;
+            const int nr = systolic_reg_rows(L.variant - 2);
             if (!encode_shell_maps(h->tm, h->f[0], fstride, h->ce, h->ca, coeffs->storage, grid->nx, grid->ny,
-                                   grid->nz, L.pitch, systolic_reg_rows(L.variant - 2), h->ws + L.xface, L.xfs,
-                                   L.nyp))
+                                   grid->nz, L.pitch, nr, face_block(nr - 1, L.eb), h->ws + L.xface, L.fxs,
+                                   h->ws + L.yface, L.fys, L.nzb))
                 return fail(FDTD_ERR_UNSUPPORTED);
         }
         fdtd_status st = upload_tiles(h, 0, 0);
@@ -781,8 +804,11 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         p.fstride = (long long)(h->L.fields[1] - h->L.fields[0]) / h->L.eb;
         p.sc = h->sc;
         p.xf = (float *)(h->ws + h->L.xface);
-        p.xfs = h->L.xfs;
-        p.nyp = h->L.nyp;
+        p.yf = (float *)(h->ws + h->L.yface);
+        p.fxs = h->L.fxs;
+        p.fys = h->L.fys;
+        p.nzb = h->L.nzb;
+        p.nzblk = h->L.nzblk;
         p.gx = h->L.gx;
         p.gy = h->L.gy;
         p.gz = h->L.gz;

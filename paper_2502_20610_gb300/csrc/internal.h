@@ -77,12 +77,15 @@ struct SysLaunch {
     float *fbase;            // f[c] == fbase + c*fstride elements for c in 0..5 when the
     long long fstride;       // arrays sit at a uniform stride (else fstride == 0)
     Scales sc;               // storage scales (16-bit formats)
-    // top x faces of the register kernel: component c of cell (x,y,z) at
-    // xf + c*xfs + x*(nz*nyp) + z*nyp + y elements, so a face (fixed x) is
-    // stored and loaded along y; the field arrays never carry them
-    float *xf;
-    long long xfs;
-    int nyp;
+    // top x and y faces of the register kernel, in z-blocks: component c of
+    // column (x, y), rows of z-block kb (of nzblk) at
+    //   x faces: xf + c*fxs + ((kb*nx + x)*ny + y)*BZ + r,
+    //   y faces: yf + c*fys + ((kb*ny + y)*nx + x)*BZ + r,
+    // BZ = the tile's z rows rounded up to 16 bytes, nzb = nzblk*BZ (the
+    // field arrays never carry these faces)
+    float *xf, *yf;
+    long long fxs, fys;
+    int nzb, nzblk;
     int gx, gy, gz;          // tile grid over skewed space sigma = p + t
     int T;                   // steps of this launch
     unsigned epoch;          // progress values of this launch are epoch + k
@@ -103,16 +106,21 @@ struct SysLaunch {
     CUtensorMap tm[3][2];
 };
 
-// Encode the shell maps of the register kernel with `nr` z rows per column:
-// lower z and y shells of the six fields (storage format `storage`, at
-// fbase + c*fstride elements) and of the FP32 coefficients ce (and ca, at any
-// 16-byte multiple after ce), rows of `pitch` elements; the lower x shell of
-// the fields from the x-face buffer xf (see SysLaunch), of the coefficients
-// from ce / ca.  One map covers all arrays of a kind (4th dimension), so one
-// bulk copy fetches a shell of all of them.  Returns false on failure.
+// Encode the shell maps of the register kernel with `nr` z rows per column
+// and z-blocks of `bz` elements: the lower z shell of the six fields (storage
+// format `storage`, at fbase + c*fstride elements, rows of `pitch`
+// elements), their lower y and x shells from the face buffers yf and xf
+// (z-block extent nzb, see SysLaunch), and the lower z, y and x shells of the
+// FP32 coefficients ce (and ca, at any 16-byte multiple after ce).  One map
+// covers all arrays of a kind (4th dimension), so one bulk copy fetches a
+// shell of all of them.  Returns false on failure.
 bool encode_shell_maps(CUtensorMap tm[3][2], void *fbase, long long fstride, const float *ce, const float *ca,
-                       int storage, int nx, int ny, int nz, int pitch, int nr, void *xf, long long xfs, int nyp);
+                       int storage, int nx, int ny, int nz, int pitch, int nr, int bz, void *xf, long long fxs,
+                       void *yf, long long fys, int nzb);
 int systolic_reg_rows(int k);
+// z-block length of the face buffers for a tile of nz_tile rows and fields of
+// eb bytes: nz_tile rounded up to a whole number of 16-byte chunks
+inline int face_block(int nz_tile, int eb) { return (nz_tile * eb + 15) / 16 * 16 / eb; }
 
 size_t systolic_smem_bytes(int variant);
 // `fmt` is a kernel format code as for the naive scheme; the shared-memory

@@ -135,9 +135,9 @@ extern "C" fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *
     p.fstride = (long long)n;
     for (int c = 0; c < 6; ++c) p.sc.s[c] = p.sc.is[c] = 1.f;  // FP32 storage
     p.sc.src = 1.f;
-    p.xf = nullptr;  // the shared-memory kernel keeps x faces in the field arrays
-    p.xfs = 0;
-    p.nyp = g.ny;
+    p.xf = p.yf = nullptr;  // the shared-memory kernel keeps its faces in the field arrays
+    p.fxs = p.fys = 0;
+    p.nzb = p.nzblk = 0;
     p.gx = gx;
     p.gy = gy;
     p.gz = gz;

@@ -23,10 +23,23 @@
 // The slot that leaves the tile at the top in x (one lane per warp) and in y
 // (one warp) is refilled each step with the lower x / y shell, and row -1
 // with the lower z shell.  All three shells of level t are fetched into a
-// shared staging buffer by six bulk tensor copies (TMA): one per shell for
-// the six fields (the field index is the 4th dimension of the copy), one per
-// shell for the coefficients.  Each thread waits on the buffer's mbarrier
-// itself.
+// shared staging buffer by bulk tensor copies (TMA): the z shell (with its x
+// and y edges) from the field arrays, the y and x shells from two face
+// buffers, one copy per shell for the six fields (the field index is a
+// dimension of the copy) and one per shell for the coefficients.  Each
+// thread waits on the buffer's mbarrier itself.
+//
+// Face buffers: the top y and x faces of a tile do not go to the field
+// arrays but to a y-face and an x-face buffer indexed by physical (x, y) and
+// by skewed z modulo a period of whole tile z-extents, in z-blocks: rows
+// 1..NZ of a column sit at consecutive addresses (rounded up to 16 bytes), at
+// a place that stays fixed for the whole life of the tile.  So the lane
+// leaving the box in x and the warp leaving it in y store their whole columns
+// with 16-byte stores, and the x lane and the y-shell warp refill theirs
+// with 16-byte shared loads.  The period is at least the grid's z extent, so
+// a wrapped position is next written only by a tile downwind of every reader
+// of the value there; rows outside the domain are neither stored nor kept
+// from a refill.
 //
 // The warp whose y slot is outside the box sits out both half-steps, so it
 // carries the tile's bookkeeping: after the second barrier it publishes the
@@ -36,13 +49,13 @@
 // step) does warp 0 wait for the upwind tiles at the start of the step, and
 // thread 0 fetch the shells then.
 //
-// Top faces: z and y faces go to the field arrays (the y face one step late,
-// from the warp whose y slot leaves, while it sits out the H half-step); the
-// x face is staged in shared memory and stored one step late, along y, into
-// a separate x-face buffer from which the downwind tile's x shell is
-// fetched.  A tile therefore publishes level t-1 after the second barrier of
-// step t.  Two block barriers per step: after the E rows are exchanged for
-// the H half-step, and after the H rows are exchanged for the E half-step.
+// Top faces: the z face goes to the field arrays at the end of each step;
+// the y face goes to the y-face buffer one step late, from the warp whose y
+// slot leaves, while it sits out the H half-step; the x face goes to the
+// x-face buffer at the end of each step.  A tile therefore publishes level
+// t-1 after the second barrier of step t.  Two block barriers per step: after
+// the E rows are exchanged for the H half-step, and after the H rows are
+// exchanged for the E half-step.
 //
 // Tile: 31 x 15 x NZ updated cells.  A step whose box lies inside the domain
 // and clear of the low walls (most steps of a large grid) runs both
@@ -82,7 +95,6 @@ struct RegTile {
     static_assert(NZ % 4 == 0, "top x face is staged with 16-byte stores");
     // shared memory, in floats
     static constexpr int XE_F = RY * NZ * 32;    // one exchanged component
-    static constexpr int XO_F = RY * 6 * NZ;
     // lower-shell staging, filled per step by bulk tensor copies (TMA) of
     // boxes whose x start is rounded down to 16 bytes (XA elements): SW =
     // 32 + XA elements cover the 32-wide x window.  One copy per shell
@@ -93,10 +105,13 @@ struct RegTile {
     static constexpr int EB = (int)sizeof(T);
     static constexpr int XA = 16 / EB, SW = 32 + XA;
     static constexpr int ZB = RY * SW;        // z shell box {SW,16,1}: [y][x]
-    static constexpr int YB = NR * SW;        // y shell box {SW,1,NR}: [z][x]
-    // x shell box of the fields, from the x-face buffer {16 + XA, NR, 1}: [z][y]
-    static constexpr int SWY = 16 + XA;
-    static constexpr int XB = NR * SWY;
+    // The top x and y faces go to two face buffers in z-blocks: rows 1..NZ of
+    // one (x, y) column of a tile sit at BZ consecutive elements (NZ rounded
+    // up to 16 bytes), so shells and faces move with 16-byte accesses.
+    static constexpr int BZ = (NZ_ * EB + 15) / 16 * 16 / EB;
+    static_assert(BZ % (16 / EB) == 0 && NZ_ % 4 == 0, "z-blocks of whole 16-byte chunks, 4 rows per access");
+    static constexpr int YB = 32 * BZ;        // y shell box {BZ,32,1} from the y-face buffer: [x][z]
+    static constexpr int XB = 16 * BZ;        // x shell box {BZ,16,1} from the x-face buffer: [y][z]
     static constexpr int XAC = 4, SWC = 36;
     static constexpr int ZBC = RY * SWC, YBC = NR * SWC, XBC = NR * 16 * XAC;
     static constexpr int NCOEF = LOSSY ? 2 : 1;   // FP32 coefficient arrays: cb (dt/eps), ca
@@ -118,13 +133,66 @@ struct RegTile {
     static constexpr size_t STG_B = OFF_XC + r128(NCOEF * 4 * (size_t)XBC);  // one buffer, bytes
     static constexpr size_t smem_bytes()
     {
-        return NBUF * STG_B + sizeof(float) * (4 * (size_t)XE_F + XO_F + NCOEF * (size_t)CE_F);
+        return NBUF * STG_B + sizeof(float) * (4 * (size_t)XE_F + NCOEF * (size_t)CE_F);
     }
 };
 
 __device__ __forceinline__ float shfl_from(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Four consecutive rows of one field as one 16-byte (FP32) or 8-byte (16-bit)
+// access: p must be aligned to it.
+template <class S>
+__device__ __forceinline__ void ld4(const typename S::T *p, float s, float &a, float &b, float &c, float &d)
+{
+    if constexpr (sizeof(typename S::T) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        a = v.x; b = v.y; c = v.z; d = v.w;
+    } else {
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
+        a = S::dec((typename S::T)(v.x & 0xffffu), s); b = S::dec((typename S::T)(v.x >> 16), s);
+        c = S::dec((typename S::T)(v.y & 0xffffu), s); d = S::dec((typename S::T)(v.y >> 16), s);
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void st4(typename S::T *p, float is, float a, float b, float c, float d)
+{
+    if constexpr (sizeof(typename S::T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    } else {
+        uint2 v;
+        v.x = (unsigned)S::enc(a, is) | ((unsigned)S::enc(b, is) << 16);
+        v.y = (unsigned)S::enc(c, is) | ((unsigned)S::enc(d, is) << 16);
+        *reinterpret_cast<uint2 *>(p) = v;
+    }
+}
+
+// Rows 1..NZ of one field of a column: loaded from a z-block, and stored into
+// one.  A store writes only the rows whose physical z (z0 + i - 1) lies in
+// the domain: with whole 16-byte chunks when all of them do, else row by row
+// (face-buffer positions of rows outside the domain belong to other cells).
+template <class S, int NR>
+__device__ __forceinline__ void ld_rows(const typename S::T *p, float s, float (&v)[NR])
+{
+#pragma unroll
+    for (int q = 0; q < (NR - 1) / 4; ++q) ld4<S>(p + 4 * q, s, v[4 * q + 1], v[4 * q + 2], v[4 * q + 3], v[4 * q + 4]);
+}
+
+template <class S, int NR>
+__device__ __forceinline__ void st_rows(typename S::T *p, float is, const float (&v)[NR], int z0, int nz)
+{
+    if (z0 >= 0 && z0 + NR - 1 <= nz) {
+#pragma unroll
+        for (int q = 0; q < (NR - 1) / 4; ++q)
+            st4<S>(p + 4 * q, is, v[4 * q + 1], v[4 * q + 2], v[4 * q + 3], v[4 * q + 4]);
+    } else {
+#pragma unroll
+        for (int i = 1; i < NR; ++i)
+            if ((unsigned)(z0 + i - 1) < (unsigned)nz) p[i - 1] = S::enc(v[i], is);
+    }
+}
 
 // Bulk tensor copy of one box of a 4D map (TMA: x, y, z, array) starting at
 // array 0 into shared memory, completing on an mbarrier; elements outside
@@ -135,6 +203,18 @@ __device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *map, int x
     asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
                  " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
                  "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(0),
+                 "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// The same for a 5D map (face buffers: z-block rows, y or x, x or y, block,
+// field), starting at field 0.
+__device__ __forceinline__ void tma_box5(void *dst, const CUtensorMap *map, int r, int a, int b, int kb,
+                                         unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<unsigned long long>(map)), "r"(r), "r"(a), "r"(b), "r"(kb), "r"(0),
                  "r"(smem_u32(bar))
                  : "memory");
 }
@@ -180,10 +260,9 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     float *const XEz = XEx + R::XE_F;
     float *const XHx = XEz + R::XE_F;      // [warp][row i-1][lane]: new H rows r = 0..NZ-1
     float *const XHz = XHx + R::XE_F;
-    float *const XO = XHz + R::XE_F;       // [warp][field 0..5][NZ]: top x face
     // dt/eps of each column, indexed by physical z mod CR: a cell's coefficient
     // stays in place while the skewed register rows move past it
-    float *const CEs = XO + R::XO_F;       // [warp][physical z mod CR][lane]
+    float *const CEs = XHz + R::XE_F;      // [warp][physical z mod CR][lane]
     float *const CAs = CEs + R::CE_F;      // the same for ca (lossy only)
     __shared__ int s_ticket, s_abort;
     __shared__ alignas(8) unsigned long long s_bar[2];  // staging barriers, one per buffer: one phase per fill
@@ -210,37 +289,31 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #define SC(c) P.sc.s[c]
 #define IS(c) P.sc.is[c]
 #define RND(v, c) S::rnd(v, SC(c), IS(c))
-// the inverse scale of field f, picked without a dynamically indexed
-// parameter array
-#define ISF(f) ((f) == 0 ? IS(0) : (f) == 1 ? IS(1) : (f) == 2 ? IS(2) : (f) == 3 ? IS(3) : (f) == 4 ? IS(4) : IS(5))
-// the staged top x face of the step whose box corner is (pbx, pby, pbz)
-#define STORE_XFACE(pbx, pby, pbz)                                                                  \
-    do {                                                                                            \
-        const int qx_ = (pbx) + TX - 1, qy_ = (pby) + q_y;                                          \
-        if (q_y < TY && (unsigned)qx_ < (unsigned)P.nx && (unsigned)qy_ < (unsigned)P.ny) {         \
-            const int wv_ = qy_ & (R::RY - 1);                                                      \
-            _Pragma("unroll") for (int k_ = 0; k_ < NPASS; ++k_) {                                  \
-                const int pr_ = q_p + 32 * k_;                                                      \
-                const int f_ = pr_ / NZ, zr_ = pr_ - f_ * NZ, qz_ = (pbz) + zr_;                    \
-                if (pr_ < NPAIR && (unsigned)qz_ < (unsigned)P.nz)                                  \
-                    XF[f_ * XFS + qx_ * XFX + qz_ * XFZ + qy_] =                                    \
-                        S::enc(XO[(wv_ * 6 + f_) * NZ + zr_], ISF(f_));                             \
-            }                                                                                       \
-        }                                                                                           \
-    } while (0)
 #define STORE6(g, i)                                                                          \
     do {                                                                                      \
         F0[g] = S::enc(ex[i], IS(0)); F1[g] = S::enc(ey[i], IS(1)); F2[g] = S::enc(ez[i], IS(2)); \
         F3[g] = S::enc(hx[i], IS(3)); F4[g] = S::enc(hy[i], IS(4)); F5[g] = S::enc(hz[i], IS(5)); \
     } while (0)
 
-    // Top x-face store into the x-face buffer, along y: thread t takes y
-    // offset t & 15 and (field, z row) pairs (t >> 4) + 32 k, so each warp
-    // writes two runs of 15 consecutive values.
+    // Face buffers: rows 1..NZ of component f of column (x, y) of a tile in
+    // z-block kb are at
+    //   x faces: XF + f*fxs + ((kb*nx + x)*ny + y)*BZ + (row - 1),
+    //   y faces: YF + f*fys + ((kb*ny + y)*nx + x)*BZ + (row - 1),
+    // kb = K mod (number of z-blocks): block kb holds skewed z (sigma_z = z +
+    // t) modulo the blocks' period, so a tile's faces and lower x / y shells
+    // keep one aligned place for its whole life, and a face (or shell) of one
+    // tile step is one contiguous run per field.  A tile's top x face is
+    // stored by the lane leaving the box in x, its top y face by the warp
+    // leaving it in y, straight from registers.
     T *const XF = reinterpret_cast<T *>(P.xf);
-    const long long XFS = P.xfs, XFZ = (long long)P.nyp, XFX = (long long)P.nyp * P.nz;
-    const int q_y = tid & 15, q_p = tid >> 4;
-    constexpr int NPAIR = 6 * NZ, NPASS = (NPAIR + 31) / 32;
+    T *const YF = reinterpret_cast<T *>(P.yf);
+    constexpr int BZ = R::BZ;
+#define FACE_STORE(dst, fs, z0)                                                             \
+    do {                                                                                    \
+        st_rows<S>((dst), IS(0), ex, (z0), P.nz); st_rows<S>((dst) + (fs), IS(1), ey, (z0), P.nz);         \
+        st_rows<S>((dst) + 2 * (fs), IS(2), ez, (z0), P.nz); st_rows<S>((dst) + 3 * (fs), IS(3), hx, (z0), P.nz); \
+        st_rows<S>((dst) + 4 * (fs), IS(4), hy, (z0), P.nz); st_rows<S>((dst) + 5 * (fs), IS(5), hz, (z0), P.nz); \
+    } while (0)
 
     constexpr int CR = R::CR;
     if (tid == 0) {
@@ -256,9 +329,9 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     // lower shells of level t into buffer b: six bulk tensor copies issued by
     // one thread (x start rounded down to 16 bytes; zero fill off the domain),
     // counted in s_niss for the final drain
-    auto issue_shells = [&](int t, int b, int Ax, int Ay, int Az) {
+    auto issue_shells = [&](int t, int b, int Ax, int Ay, int Az, int kb) {
         const int bx = Ax - t, by = Ay - t, bz = Az - t;
-        const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1), y0 = by & ~(XA - 1);
+        const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1);
         char *sb = stg0 + (size_t)b * R::STG_B;
         unsigned long long *bar = &s_bar[b];
         // order this thread's view of the upwind tiles' global stores (generic
@@ -267,9 +340,9 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
         asm volatile("fence.proxy.async.global;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                      "r"(R::TMA_BYTES) : "memory");
-        tma_box(sb, &P.tm[0][0], x0, by - 1, bz - 1, bar);
-        tma_box(sb + R::OFF_Y, &P.tm[1][0], x0, by - 1, bz - 1, bar);
-        tma_box(sb + R::OFF_X, &P.tm[2][0], y0, bz - 1, bx - 1, bar);
+        tma_box(sb, &P.tm[0][0], x0, by - 1, bz - 1, bar);              // z shell: field arrays
+        tma_box5(sb + R::OFF_Y, &P.tm[1][0], 0, bx, by - 1, kb, bar);        // y shell: y-face buffer
+        tma_box5(sb + R::OFF_X, &P.tm[2][0], 0, by - 1, bx - 1, kb, bar);    // x shell: x-face buffer
         tma_box(sb + R::OFF_ZC, &P.tm[0][1], x0c, by - 1, bz - 1, bar);
         tma_box(sb + R::OFF_YC, &P.tm[1][1], x0c, by - 1, bz - 1, bar);
         tma_box(sb + R::OFF_XC, &P.tm[2][1], x0c, by, bz - 1, bar);
@@ -293,6 +366,9 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
         const int tile = P.tiles[ticket];
         const int I = tile % P.gx, J = (tile / P.gx) % P.gy, K = tile / (P.gx * P.gy);
         const int Ax = I * TX, Ay = J * TY, Az = K * TZ;
+        const int kb = K % P.nzblk;  // this tile's z-block in the face buffers
+        T *const XFk = XF + (long long)kb * P.nx * P.ny * BZ;
+        T *const YFk = YF + (long long)kb * P.nx * P.ny * BZ;
         const Interval iv = tile_interval<TX, TY, TZ>(P, I, J, K);
         Upwind U;
         upwind_of<TX, TY, TZ>(P, I, J, K, U);
@@ -316,22 +392,28 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             const int bx = Ax - iv.s, by = Ay - iv.s;
             const int px = bx + ((lane - bx) & 31), py = by + ((w - by) & (R::RY - 1));
             const bool cin = (unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny;
-            // the lower x shell column at level start-1: written by the left
-            // tiles into the x-face buffer during this launch (start >= 1), or
-            // the launch's initial state in the field arrays (start = 0)
+            // rows 1..NZ of the lower x shell column and of the lower y shell
+            // row at level start-1: written by the upwind tiles into the face
+            // buffers during this launch (start >= 1; the x-face buffer holds
+            // the corner column), else the launch's initial state in the
+            // field arrays (start = 0); row 0 is the lower z shell
             const bool xshell = px == bx && iv.s > 0;
+            const bool yshell = py == by && iv.s > 0 && !xshell;
             const long long col = px + (long long)P.pitch * py;
+            const T *const fq = xshell ? XFk + ((long long)px * P.ny + py) * BZ
+                                       : YFk + ((long long)py * P.nx + px) * BZ;
+            const long long fqs = xshell ? P.fxs : P.fys;
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
                 const int pz = Az + i - 1 - iv.s + 1;
                 float c = 0.f, a = 0.f;
                 if (cin && (unsigned)pz < (unsigned)P.nz) {
                     const long long g = col + sxy * pz;
-                    if (xshell) {  // the left tiles' top x face of level start-1
-                        const long long q = px * XFX + pz * XFZ + py;
-                        ex[i] = S::dec(S::ld_cg(XF + q), SC(0)); ey[i] = S::dec(S::ld_cg(XF + XFS + q), SC(1));
-                        ez[i] = S::dec(S::ld_cg(XF + 2 * XFS + q), SC(2)); hx[i] = S::dec(S::ld_cg(XF + 3 * XFS + q), SC(3));
-                        hy[i] = S::dec(S::ld_cg(XF + 4 * XFS + q), SC(4)); hz[i] = S::dec(S::ld_cg(XF + 5 * XFS + q), SC(5));
+                    if (i > 0 && (xshell || yshell)) {  // the upwind tiles' top x / y face of level start-1
+                        const T *q = fq + (i - 1);
+                        ex[i] = S::dec(S::ld_cg(q), SC(0)); ey[i] = S::dec(S::ld_cg(q + fqs), SC(1));
+                        ez[i] = S::dec(S::ld_cg(q + 2 * fqs), SC(2)); hx[i] = S::dec(S::ld_cg(q + 3 * fqs), SC(3));
+                        hy[i] = S::dec(S::ld_cg(q + 4 * fqs), SC(4)); hz[i] = S::dec(S::ld_cg(q + 5 * fqs), SC(5));
                     } else {
                         ex[i] = S::dec(S::ld_cg(F0 + g), SC(0)); ey[i] = S::dec(S::ld_cg(F1 + g), SC(1));
                         ez[i] = S::dec(S::ld_cg(F2 + g), SC(2)); hx[i] = S::dec(S::ld_cg(F3 + g), SC(3));
@@ -381,6 +463,12 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             // box cell is updated with no mask.  (The x-shell lane and the
             // y-shell warp compute values that their refills overwrite.)
             const bool inner = bx >= 1 && by >= 1 && bz >= 1 && bx + TX <= P.nx && by + TY <= P.ny && bz + TZ <= P.nz;
+            // every row of the box's z range lies in the domain (rows refilled
+            // from the face buffers need no clearing)
+            const bool zin = bz >= 0 && bz + TZ <= P.nz;
+            // physical x of this lane's column after the refills (the x-shell
+            // lane moves to bx - 1)
+            const int xw = (bx - 1) + ((lane - bx + 1) & 31);
 
             // A. publish E^t (old) rows for the warp below's H half-step
 #pragma unroll
@@ -402,31 +490,20 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 __syncthreads();
                 if (s_abort) { abort = true; break; }
             }
-            if (pst != 1 && tid == 0) issue_shells(t, cur, Ax, Ay, Az);
+            if (pst != 1 && tid == 0) issue_shells(t, cur, Ax, Ay, Az, kb);
 
             // B. the warp whose y slot leaves the tile this step is idle during
             //    the H half-step: it stores last step's top y face, which its
-            //    registers still hold; all threads store the staged top x face
+            //    registers still hold, into the y-face buffer
             if (w == yf_w && t > iv.s) {
                 const int pbx = bx + 1, pby = by + 1, pbz = bz + 1;  // box corner of step t-1
                 const int pdx = (lane - pbx) & 31;
                 const int qx = pbx + pdx, qy = pby + TY - 1;
-                if (pdx < TX && (unsigned)qx < (unsigned)P.nx && (unsigned)qy < (unsigned)P.ny) {
-                    const long long c2 = qx + (long long)P.pitch * qy;
-                    // (the top row, i = NR - 1, went out with the top z face)
-#pragma unroll
-                    for (int i = 1; i < NR - 1; ++i) {
-                        const int qz = pbz + i - 1;
-                        if ((unsigned)qz < (unsigned)P.nz) {
-                            const long long g = c2 + sxy * qz;
-                            STORE6(g, i);
-                        }
-                    }
-                }
+                if (pdx < TX && (unsigned)qx < (unsigned)P.nx && (unsigned)qy < (unsigned)P.ny)
+                    FACE_STORE(YFk + ((long long)qy * P.nx + qx) * BZ, P.fys, pbz);
             }
-            if (t > iv.s) STORE_XFACE(bx + 1, by + 1, bz + 1);  // top x face of step t-1, staged in XO
-            // x / y starts of the staged boxes (rounded down to 16 bytes)
-            const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1), y0 = by & ~(XA - 1);
+            // x start of the staged z shell (rounded down to 16 bytes)
+            const int x0 = (bx - 1) & ~(XA - 1), x0c = (bx - 1) & ~(R::XAC - 1);
 
             // C. H half-step, top-down in place: H[i] <- H[i-1] - dt curl_f(E[i-1], E[i], ...)
             if (ybox) {
@@ -465,39 +542,63 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             // D. refills from the staged shells, then publish new H rows for the
             //    warp above's E half-step
             const int xec = (bx - 1) - x0c;  // x offset of the coefficient shell column in its chunk
+            // rows of a refilled column whose physical z lies outside the
+            // domain: the face buffers hold other cells' values there
+#define CLEAR_OUT_ROWS(a, b, c)                                                          \
+    do {                                                                                 \
+        if (!zin) {                                                                      \
+            _Pragma("unroll") for (int i_ = 1; i_ < NR; ++i_) if (i_ < i_lo || i_ >= i_hi) \
+                a[i_] = b[i_] = c[i_] = 0.f;                                               \
+        }                                                                                \
+    } while (0)
             if (w == ey_w) {  // the y shell warp takes its whole column set (level t)
-                const int xw = (bx - 1) + ((lane - bx + 1) & 31);
+                // row 0 from the lower z shell (its row y = by - 1); rows
+                // 1..NZ from the y-face shell (x = bx .. bx+30) or, in the
+                // corner lane (x = bx - 1), from the x-face shell's row by - 1
                 const int xl = xw - x0, xlc = xw - x0c;
+                ex[0] = S::dec(ZST[0 * R::ZB + xl], SC(0));
+                ey[0] = S::dec(ZST[1 * R::ZB + xl], SC(1));
+                ez[0] = S::dec(ZST[2 * R::ZB + xl], SC(2));
+                hx[0] = S::dec(ZST[3 * R::ZB + xl], SC(3));
+                hy[0] = S::dec(ZST[4 * R::ZB + xl], SC(4));
+                hz[0] = S::dec(ZST[5 * R::ZB + xl], SC(5));
+                const bool corner = xw == bx - 1;
+                const T *src = corner ? XST : YST + (xw - bx) * BZ;
+                const int fst = corner ? R::XB : R::YB;
+                ld_rows<S>(src, SC(0), ex);
+                ld_rows<S>(src + fst, SC(1), ey);
+                ld_rows<S>(src + 2 * fst, SC(2), ez);
+                ld_rows<S>(src + 3 * fst, SC(3), hx);
+                ld_rows<S>(src + 4 * fst, SC(4), hy);
+                ld_rows<S>(src + 5 * fst, SC(5), hz);
+                CLEAR_OUT_ROWS(ex, ey, ez);
+                CLEAR_OUT_ROWS(hx, hy, hz);
 #pragma unroll
                 for (int i = 0; i < NR; ++i) {
-                    ex[i] = S::dec(YST[0 * R::YB + i * SW + xl], SC(0));
-                    ey[i] = S::dec(YST[1 * R::YB + i * SW + xl], SC(1));
-                    ez[i] = S::dec(YST[2 * R::YB + i * SW + xl], SC(2));
-                    hx[i] = S::dec(YST[3 * R::YB + i * SW + xl], SC(3));
-                    hy[i] = S::dec(YST[4 * R::YB + i * SW + xl], SC(4));
-                    hz[i] = S::dec(YST[5 * R::YB + i * SW + xl], SC(5));
                     CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YSC[i * SWC + xlc];
                     if (R::LOSSY) CAs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = YSA[i * SWC + xlc];
                 }
             } else if (!ybox) {  // the previous top y row (two outside slots): kept
-            } else if (xbox) {  // row -1 takes the lower z shell's H and coefficient
-                const int o = (dy + 1) * SW + (px - x0), oc = (dy + 1) * SWC + (px - x0c);
+            } else {  // every lane's row -1 takes the lower z shell's H and coefficient
+                const int o = (dy + 1) * SW + (xw - x0), oc = (dy + 1) * SWC + (xw - x0c);
                 hx[0] = S::dec(ZST[3 * R::ZB + o], SC(3));
                 hy[0] = S::dec(ZST[4 * R::ZB + o], SC(4));
                 hz[0] = S::dec(ZST[5 * R::ZB + o], SC(5));
                 CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZSC[oc];
                 if (R::LOSSY) CAs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZSA[oc];
-            } else {  // the lane leaving the tile in x takes the x shell's H and coefficient
-                const T *xs = XST + (by + dy - y0);
-                const float *xsc = XSC + dy * R::XAC + xec;
-                const float *xsa = XSA + dy * R::XAC + xec;
+                if (!xbox) {  // the lane leaving the tile in x: rows 1..NZ of H from the x-face shell
+                    const T *xs = XST + (dy + 1) * BZ;
+                    ld_rows<S>(xs + 3 * R::XB, SC(3), hx);
+                    ld_rows<S>(xs + 4 * R::XB, SC(4), hy);
+                    ld_rows<S>(xs + 5 * R::XB, SC(5), hz);
+                    CLEAR_OUT_ROWS(hx, hy, hz);
+                    const float *xsc = XSC + dy * R::XAC + xec;
+                    const float *xsa = XSA + dy * R::XAC + xec;
 #pragma unroll
-                for (int i = 0; i < NR; ++i) {
-                    hx[i] = S::dec(xs[3 * R::XB + i * R::SWY], SC(3));
-                    hy[i] = S::dec(xs[4 * R::XB + i * R::SWY], SC(4));
-                    hz[i] = S::dec(xs[5 * R::XB + i * R::SWY], SC(5));
-                    CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xsc[i * 16 * R::XAC];
-                    if (R::LOSSY) CAs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xsa[i * 16 * R::XAC];
+                    for (int i = 1; i < NR; ++i) {
+                        CEs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xsc[i * 16 * R::XAC];
+                        if (R::LOSSY) CAs[(w * CR + ((bz - 1 + i) & (CR - 1))) * 32 + lane] = xsa[i * 16 * R::XAC];
+                    }
                 }
             }
 #pragma unroll
@@ -518,7 +619,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 const bool nxt = t + 1 <= iv.e && level_ready(P, U, s_seen, t + 1);
                 __syncwarp();  // orders lanes 1, 2's acquires before lane 0's copies
                 if (lane == 0) {
-                    if (R::NBUF == 2 && nxt) issue_shells(t + 1, cur ^ 1, Ax, Ay, Az);
+                    if (R::NBUF == 2 && nxt) issue_shells(t + 1, cur ^ 1, Ax, Ay, Az, kb);
                     s_pref = nxt ? (R::NBUF == 2 ? 1 : 2) : 0;
                 }
             }
@@ -579,19 +680,18 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     e_pass(std::bool_constant<S::narrow>(), std::false_type());
                 else
                     e_pass(std::bool_constant<S::narrow>(), std::true_type());
-                if (xbox) {  // row -1 takes the lower z shell's E (level t)
-                    const int o = (dy + 1) * SW + (px - x0);
+                {  // every lane's row -1 takes the lower z shell's E (level t)
+                    const int o = (dy + 1) * SW + (xw - x0);
                     ex[0] = S::dec(ZST[0 * R::ZB + o], SC(0));
                     ey[0] = S::dec(ZST[1 * R::ZB + o], SC(1));
                     ez[0] = S::dec(ZST[2 * R::ZB + o], SC(2));
-                } else {  // the x lane takes the rest of its shell column
-                    const T *xs = XST + (by + dy - y0);
-#pragma unroll
-                    for (int i = 0; i < NR; ++i) {
-                        ex[i] = S::dec(xs[0 * R::XB + i * R::SWY], SC(0));
-                        ey[i] = S::dec(xs[1 * R::XB + i * R::SWY], SC(1));
-                        ez[i] = S::dec(xs[2 * R::XB + i * R::SWY], SC(2));
-                    }
+                }
+                if (!xbox) {  // the x lane: rows 1..NZ of E from the x-face shell
+                    const T *xs = XST + (dy + 1) * BZ;
+                    ld_rows<S>(xs, SC(0), ex);
+                    ld_rows<S>(xs + R::XB, SC(1), ey);
+                    ld_rows<S>(xs + 2 * R::XB, SC(2), ez);
+                    CLEAR_OUT_ROWS(ex, ey, ez);
                 }
             }
 
@@ -639,47 +739,22 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     STORE6(g, NR - 1);
                 }
             }
-            if (ybox && dx == TX - 1) {  // top x face: staged, stored into the x-face buffer next step
-                float *xo = XO + w * 6 * NZ;
-#pragma unroll
-                for (int k = 0; k < NZ / 4; ++k) {
-                    *reinterpret_cast<float4 *>(xo + 0 * NZ + 4 * k) =
-                        make_float4(ex[4 * k + 1], ex[4 * k + 2], ex[4 * k + 3], ex[4 * k + 4]);
-                    *reinterpret_cast<float4 *>(xo + 1 * NZ + 4 * k) =
-                        make_float4(ey[4 * k + 1], ey[4 * k + 2], ey[4 * k + 3], ey[4 * k + 4]);
-                    *reinterpret_cast<float4 *>(xo + 2 * NZ + 4 * k) =
-                        make_float4(ez[4 * k + 1], ez[4 * k + 2], ez[4 * k + 3], ez[4 * k + 4]);
-                    *reinterpret_cast<float4 *>(xo + 3 * NZ + 4 * k) =
-                        make_float4(hx[4 * k + 1], hx[4 * k + 2], hx[4 * k + 3], hx[4 * k + 4]);
-                    *reinterpret_cast<float4 *>(xo + 4 * NZ + 4 * k) =
-                        make_float4(hy[4 * k + 1], hy[4 * k + 2], hy[4 * k + 3], hy[4 * k + 4]);
-                    *reinterpret_cast<float4 *>(xo + 5 * NZ + 4 * k) =
-                        make_float4(hz[4 * k + 1], hz[4 * k + 2], hz[4 * k + 3], hz[4 * k + 4]);
-                }
-            }
+            // top x face (all rows of the lane leaving the box in x) into the
+            // x-face buffer, where the downwind tile's x shell is fetched
+            if (ybox && dx == TX - 1 && (unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny)
+                FACE_STORE(XFk + ((long long)px * P.ny + py) * BZ, P.fxs, bz);
         }
         if (abort) break;
-        // the last step's top y face and staged top x face, then its progress
+        // the last step's top y face (the launch's last one included: the
+        // downwind tile reads it from the y-face buffer), then its progress
         __syncthreads();
-        if (iv.e < P.T - 1) {
+        {
             const int pbx = Ax - iv.e, pby = Ay - iv.e, pbz = Az - iv.e;
             const int pdx = (lane - pbx) & 31, pdy = (w - pby) & (R::RY - 1);
             const int qx = pbx + pdx, qy = pby + pdy;
-            if (pdy == TY - 1 && pdx < TX && (unsigned)qx < (unsigned)P.nx && (unsigned)qy < (unsigned)P.ny) {
-                const long long c2 = qx + (long long)P.pitch * qy;
-#pragma unroll
-                for (int i = 1; i < NR; ++i) {
-                    const int qz = pbz + i - 1;
-                    if ((unsigned)qz < (unsigned)P.nz) {
-                        const long long g = c2 + sxy * qz;
-                        STORE6(g, i);
-                    }
-                }
-            }
+            if (pdy == TY - 1 && pdx < TX && (unsigned)qx < (unsigned)P.nx && (unsigned)qy < (unsigned)P.ny)
+                FACE_STORE(YFk + ((long long)qy * P.nx + qx) * BZ, P.fys, pbz);
         }
-        // the downwind tile reads the x face of every level, the launch's last
-        // one included, from the x-face buffer
-        STORE_XFACE(Ax - iv.e, Ay - iv.e, Az - iv.e);
         __syncthreads();
         if (tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.e + 1u);
     }
@@ -703,8 +778,8 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #undef IS
 #undef RND
 #undef STORE6
-#undef STORE_XFACE
-#undef ISF
+#undef FACE_STORE
+#undef CLEAR_OUT_ROWS
 
 // 31 x 15 x 12 and 31 x 15 x 8 tiles, each for every kernel format; the
 // lossy (absorber) form for the 31 x 15 x 12 tile

@@ -84,10 +84,11 @@ def test_autograd_and_finite_differences(cuda_device):
     voxels = [np.unravel_index(int(v), eps_box.shape) for v in order[:16]]
     assert len(set(voxels)) == 16
     worst = 0.0
+    eps64 = np.asarray(eps_box, np.float64)  # perturb in FP64 (a float32 step would be rounded)
     for q in voxels:
         q = tuple(int(v) for v in q)
-        h = 1e-5 * eps_box[q]  # truncation error ~(h/eps)^2 stays far below the tolerance
-        ep, em = eps_box.copy(), eps_box.copy()
+        h = 1e-5 * eps64[q]  # truncation error ~(h/eps)^2 stays far below the tolerance
+        ep, em = eps64.copy(), eps64.copy()
         ep[q] += h
         em[q] -= h
         fd = (adj.objective(p.shape, p.eps_with(ep), f0, p.n_steps, [(c, i, j, k, J)], obj, DT) -
