@@ -9,6 +9,10 @@
 // registers as FP32 numbers that are already rounded this way (rnd), so both
 // schedules hold the same values at every step and stay bit-identical.
 //
+// Two values are rounded together where the kernels allow it (rnd2, enc2):
+// one packed conversion instruction rounds both, each to nearest even exactly
+// as the scalar conversion does, so the results are the same bits.
+//
 // When all six scales are equal (s), the update is linear and homogeneous in
 // the fields, so the kernels step the stored values q = v / s directly (the
 // "uniform" formats): no scaling on load or store, and point-source
@@ -34,8 +38,30 @@ struct StoreF32 {
     __device__ __forceinline__ static float dec(T q, float) { return q; }
     __device__ __forceinline__ static T enc(float v, float) { return v; }
     __device__ __forceinline__ static float rnd(float v, float, float) { return v; }
+    __device__ __forceinline__ static void rnd2(float &, float &, float, float) {}
     __device__ __forceinline__ static T ld_cg(const T *p) { return __ldcg(p); }
 };
+
+// Packed round trips of the 16-bit formats: q = fl16(a'), fl16(b') by one
+// cvt.rn.{f16,bf16}x2.f32, then both decoded.
+__device__ __forceinline__ unsigned pack_f16(float a, float b)
+{
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const unsigned *>(&h);
+}
+__device__ __forceinline__ unsigned pack_bf16(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const unsigned *>(&h);
+}
+__device__ __forceinline__ float2 unpack_f16(unsigned u)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(&u));
+}
+__device__ __forceinline__ float2 unpack_bf16(unsigned u)
+{
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+}
 
 struct StoreF16 {
     using T = unsigned short;  // IEEE binary16 bits
@@ -45,6 +71,16 @@ struct StoreF16 {
     __device__ __forceinline__ static float dec(T q, float s) { return __fmul_rn(__half2float(__ushort_as_half(q)), s); }
     __device__ __forceinline__ static T enc(float v, float inv_s) { return __half_as_ushort(__float2half_rn(__fmul_rn(v, inv_s))); }
     __device__ __forceinline__ static float rnd(float v, float s, float inv_s) { return dec(enc(v, inv_s), s); }
+    __device__ __forceinline__ static unsigned enc2(float a, float b, float inv_s)
+    {
+        return pack_f16(__fmul_rn(a, inv_s), __fmul_rn(b, inv_s));
+    }
+    __device__ __forceinline__ static void rnd2(float &a, float &b, float s, float inv_s)
+    {
+        const float2 f = unpack_f16(enc2(a, b, inv_s));
+        a = __fmul_rn(f.x, s);
+        b = __fmul_rn(f.y, s);
+    }
     __device__ __forceinline__ static T ld_cg(const T *p) { return __ldcg(p); }
 };
 
@@ -62,6 +98,16 @@ struct StoreBF16 {
         return __bfloat16_as_ushort(__float2bfloat16_rn(__fmul_rn(v, inv_s)));
     }
     __device__ __forceinline__ static float rnd(float v, float s, float inv_s) { return dec(enc(v, inv_s), s); }
+    __device__ __forceinline__ static unsigned enc2(float a, float b, float inv_s)
+    {
+        return pack_bf16(__fmul_rn(a, inv_s), __fmul_rn(b, inv_s));
+    }
+    __device__ __forceinline__ static void rnd2(float &a, float &b, float s, float inv_s)
+    {
+        const float2 f = unpack_bf16(enc2(a, b, inv_s));
+        a = __fmul_rn(f.x, s);
+        b = __fmul_rn(f.y, s);
+    }
     __device__ __forceinline__ static T ld_cg(const T *p) { return __ldcg(p); }
 };
 
@@ -74,6 +120,13 @@ struct StoreF16U {
     __device__ __forceinline__ static float dec(T q, float) { return __half2float(__ushort_as_half(q)); }
     __device__ __forceinline__ static T enc(float v, float) { return __half_as_ushort(__float2half_rn(v)); }
     __device__ __forceinline__ static float rnd(float v, float, float) { return __half2float(__float2half_rn(v)); }
+    __device__ __forceinline__ static unsigned enc2(float a, float b, float) { return pack_f16(a, b); }
+    __device__ __forceinline__ static void rnd2(float &a, float &b, float, float)
+    {
+        const float2 f = unpack_f16(pack_f16(a, b));
+        a = f.x;
+        b = f.y;
+    }
     __device__ __forceinline__ static T ld_cg(const T *p) { return __ldcg(p); }
 };
 
@@ -87,6 +140,13 @@ struct StoreBF16U {
     __device__ __forceinline__ static float rnd(float v, float, float)
     {
         return __bfloat162float(__float2bfloat16_rn(v));
+    }
+    __device__ __forceinline__ static unsigned enc2(float a, float b, float) { return pack_bf16(a, b); }
+    __device__ __forceinline__ static void rnd2(float &a, float &b, float, float)
+    {
+        const float2 f = unpack_bf16(pack_bf16(a, b));
+        a = f.x;
+        b = f.y;
     }
     __device__ __forceinline__ static T ld_cg(const T *p) { return __ldcg(p); }
 };

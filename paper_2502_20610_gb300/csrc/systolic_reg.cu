@@ -92,7 +92,7 @@ struct RegTile {
     static constexpr int TX = 31, TY = TY_, TZ = NZ_;
     static_assert(TY_ == RY - 1 || TY_ == RY - 2, "one or two y slots outside the box");
     static_assert(NR <= 16 && TY <= 16, "cooperative entries: row < 16, warp offset < 16");
-    static_assert(NZ % 4 == 0, "top x face is staged with 16-byte stores");
+    static_assert(NZ % 4 == 0, "rows move in groups of four (16-byte accesses) and pairs (packed rounding)");
     // shared memory, in floats
     static constexpr int XE_F = RY * NZ * 32;    // one exchanged component
     // lower-shell staging, filled per step by bulk tensor copies (TMA) of
@@ -163,8 +163,8 @@ __device__ __forceinline__ void st4(typename S::T *p, float is, float a, float b
         *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
     } else {
         uint2 v;
-        v.x = (unsigned)S::enc(a, is) | ((unsigned)S::enc(b, is) << 16);
-        v.y = (unsigned)S::enc(c, is) | ((unsigned)S::enc(d, is) << 16);
+        v.x = S::enc2(a, b, is);
+        v.y = S::enc2(c, d, is);
         *reinterpret_cast<uint2 *>(p) = v;
     }
 }
@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #define SC(c) P.sc.s[c]
 #define IS(c) P.sc.is[c]
 #define RND(v, c) S::rnd(v, SC(c), IS(c))
+#define RND2(a, b, c) S::rnd2(a, b, SC(c), IS(c))
 #define STORE6(g, i)                                                                          \
     do {                                                                                      \
         F0[g] = S::enc(ex[i], IS(0)); F1[g] = S::enc(ey[i], IS(1)); F2[g] = S::enc(ez[i], IS(2)); \
@@ -509,20 +510,35 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             if (ybox) {
                 const int wn = (w + 1) & (R::RY - 1);
                 const int src = (lane + 1) & 31;
+                // rows in pairs (i, i-1), both computed from the old values
+                // before either is written, so 16-bit storage rounds two new
+                // values with one packed conversion
                 auto h_pass = [&](auto masked) {
 #pragma unroll
-                    for (int i = NR - 1; i >= 1; --i) {
-                        const float ez_xp = shfl_from(ez[i - 1], src);
-                        const float ey_xp = shfl_from(ey[i - 1], src);
-                        const float ez_yp = XEz[(wn * NZ + (i - 1)) * 32 + lane];
-                        const float ex_yp = XEx[(wn * NZ + (i - 1)) * 32 + lane];
-                        const float nhx = h_x(hx[i - 1], ez_yp, ez[i - 1], ey[i], ey[i - 1], ndt);
-                        const float nhy = h_y(hy[i - 1], ex[i], ex[i - 1], ez_xp, ez[i - 1], ndt);
-                        const float nhz = h_z(hz[i - 1], ey_xp, ey[i - 1], ex_yp, ex[i - 1], ndt);
-                        const bool upd = !decltype(masked)::value || (colin && i >= i_lo && i < i_hi);
-                        hx[i] = upd ? RND(nhx, 3) : hx[i - 1];
-                        hy[i] = upd ? RND(nhy, 4) : hy[i - 1];
-                        hz[i] = upd ? RND(nhz, 5) : hz[i - 1];
+                    for (int i = NR - 1; i >= 2; i -= 2) {
+                        float nh[2][3];
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const int r = i - k;
+                            const float ez_xp = shfl_from(ez[r - 1], src);
+                            const float ey_xp = shfl_from(ey[r - 1], src);
+                            const float ez_yp = XEz[(wn * NZ + (r - 1)) * 32 + lane];
+                            const float ex_yp = XEx[(wn * NZ + (r - 1)) * 32 + lane];
+                            nh[k][0] = h_x(hx[r - 1], ez_yp, ez[r - 1], ey[r], ey[r - 1], ndt);
+                            nh[k][1] = h_y(hy[r - 1], ex[r], ex[r - 1], ez_xp, ez[r - 1], ndt);
+                            nh[k][2] = h_z(hz[r - 1], ey_xp, ey[r - 1], ex_yp, ex[r - 1], ndt);
+                        }
+                        RND2(nh[0][0], nh[1][0], 3);
+                        RND2(nh[0][1], nh[1][1], 4);
+                        RND2(nh[0][2], nh[1][2], 5);
+                        const bool u0 = !decltype(masked)::value || (colin && i >= i_lo && i < i_hi);
+                        const bool u1 = !decltype(masked)::value || (colin && i - 1 >= i_lo && i - 1 < i_hi);
+                        const float a0 = u0 ? nh[0][0] : hx[i - 1], b0 = u0 ? nh[0][1] : hy[i - 1],
+                                    c0 = u0 ? nh[0][2] : hz[i - 1];
+                        const float a1 = u1 ? nh[1][0] : hx[i - 2], b1 = u1 ? nh[1][1] : hy[i - 2],
+                                    c1 = u1 ? nh[1][2] : hz[i - 2];
+                        hx[i] = a0; hy[i] = b0; hz[i] = c0;
+                        hx[i - 1] = a1; hy[i - 1] = b1; hz[i - 1] = c1;
                     }
                 };
                 if (inner)
@@ -643,32 +659,44 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 const bool ux = py > 0, uy = px > 0, uz = px > 0 && py > 0;
                 auto e_pass = [&](auto round, auto masked) {
 #pragma unroll
-                    for (int i = NR - 1; i >= 1; --i) {
-                        const float hz_xm = shfl_from(hz[i], src);
-                        const float hy_xm = shfl_from(hy[i], src);
-                        const float hx_ym = XHx[(wm * NZ + (i - 1)) * 32 + lane];
-                        const float hz_ym = XHz[(wm * NZ + (i - 1)) * 32 + lane];
-                        const float c = CEs[(w * CR + ((bz + i - 1) & (CR - 1))) * 32 + lane];
-                        const float a = R::LOSSY ? CAs[(w * CR + ((bz + i - 1) & (CR - 1))) * 32 + lane] : 1.f;
-                        float nex = e_x(decay<R::LOSSY>(a, ex[i - 1]), hz[i], hz_ym, hy[i], hy[i - 1], c);
-                        float ney = e_y(decay<R::LOSSY>(a, ey[i - 1]), hx[i], hx[i - 1], hz[i], hz_xm, c);
-                        float nez = e_z(decay<R::LOSSY>(a, ez[i - 1]), hy[i], hy_xm, hx[i], hx_ym, c);
+                    for (int i = NR - 1; i >= 2; i -= 2) {
+                        float ne[2][3];
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const int r = i - k;
+                            const float hz_xm = shfl_from(hz[r], src);
+                            const float hy_xm = shfl_from(hy[r], src);
+                            const float hx_ym = XHx[(wm * NZ + (r - 1)) * 32 + lane];
+                            const float hz_ym = XHz[(wm * NZ + (r - 1)) * 32 + lane];
+                            const float c = CEs[(w * CR + ((bz + r - 1) & (CR - 1))) * 32 + lane];
+                            const float a = R::LOSSY ? CAs[(w * CR + ((bz + r - 1) & (CR - 1))) * 32 + lane] : 1.f;
+                            ne[k][0] = e_x(decay<R::LOSSY>(a, ex[r - 1]), hz[r], hz_ym, hy[r], hy[r - 1], c);
+                            ne[k][1] = e_y(decay<R::LOSSY>(a, ey[r - 1]), hx[r], hx[r - 1], hz[r], hz_xm, c);
+                            ne[k][2] = e_z(decay<R::LOSSY>(a, ez[r - 1]), hy[r], hy_xm, hx[r], hx_ym, c);
+                        }
                         if (decltype(round)::value) {
-                            nex = RND(nex, 0);
-                            ney = RND(ney, 1);
-                            nez = RND(nez, 2);
+                            RND2(ne[0][0], ne[1][0], 0);
+                            RND2(ne[0][1], ne[1][1], 1);
+                            RND2(ne[0][2], ne[1][2], 2);
                         }
-                        if (decltype(masked)::value) {
-                            const bool in = colin && i >= i_lo && i < i_hi;
-                            const bool kz = bz + i - 1 > 0;
-                            ex[i] = (in && ux && kz) ? nex : ex[i - 1];
-                            ey[i] = (in && uy && kz) ? ney : ey[i - 1];
-                            ez[i] = (in && uz) ? nez : ez[i - 1];
-                        } else {
-                            ex[i] = nex;
-                            ey[i] = ney;
-                            ez[i] = nez;
+                        float o[2][3];
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const int r = i - k;
+                            if (decltype(masked)::value) {
+                                const bool in = colin && r >= i_lo && r < i_hi;
+                                const bool kz = bz + r - 1 > 0;
+                                o[k][0] = (in && ux && kz) ? ne[k][0] : ex[r - 1];
+                                o[k][1] = (in && uy && kz) ? ne[k][1] : ey[r - 1];
+                                o[k][2] = (in && uz) ? ne[k][2] : ez[r - 1];
+                            } else {
+                                o[k][0] = ne[k][0];
+                                o[k][1] = ne[k][1];
+                                o[k][2] = ne[k][2];
+                            }
                         }
+                        ex[i] = o[0][0]; ey[i] = o[0][1]; ez[i] = o[0][2];
+                        ex[i - 1] = o[1][0]; ey[i - 1] = o[1][1]; ez[i - 1] = o[1][2];
                     }
                 };
                 // 16-bit storage rounds each new E value here, except in the
@@ -714,10 +742,10 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             }
             if (S::narrow && srcthr) {  // one rounding per value, as the naive schedule stores it
 #pragma unroll
-                for (int i = 1; i < NR; ++i) {
-                    ex[i] = RND(ex[i], 0);
-                    ey[i] = RND(ey[i], 1);
-                    ez[i] = RND(ez[i], 2);
+                for (int i = 1; i < NR; i += 2) {
+                    RND2(ex[i], ex[i + 1], 0);
+                    RND2(ey[i], ey[i + 1], 1);
+                    RND2(ez[i], ez[i + 1], 2);
                 }
             }
 
@@ -777,6 +805,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
 #undef SC
 #undef IS
 #undef RND
+#undef RND2
 #undef STORE6
 #undef FACE_STORE
 #undef CLEAR_OUT_ROWS
