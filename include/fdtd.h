@@ -79,7 +79,14 @@ typedef struct {
     float field_scale[6];     /* 16-bit storage: s_c, a power of two in [2^-100, 2^100], 0 = 1;
                                  unused for F32.  Equal scales are fastest. */
     int32_t tile[3];          /* systolic subdomain (updated cells per axis); 0 = default */
-    int32_t cluster[3];       /* systolic cluster shape; 0 = default (1,1,1) */
+    int32_t cluster[3];       /* systolic thread-block cluster shape in tiles; 0 = 1.
+                                 (1,1,1): every tile in its own CTA, all faces between
+                                 tiles through global memory (Sec. 3, Sec. 4).
+                                 (2,1,1): x pairs of the default 31x15x12 tile share a
+                                 2-CTA cluster; the upwind tile hands its top x face to
+                                 the downwind one through distributed shared memory,
+                                 the pair's outer faces go through global memory.
+                                 Lossless boundaries only; other shapes UNSUPPORTED. */
     double wait_timeout_s;    /* bound on any device-side wait; <= 0 = 2 s */
     int32_t max_source_steps; /* capacity of each source table; <= 0 = 65536 */
     int32_t steps_per_launch; /* systolic: steps per persistent launch; <= 0 = 1024 */

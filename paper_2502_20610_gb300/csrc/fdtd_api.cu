@@ -37,6 +37,7 @@ struct Layout {
     int eb;     // bytes per stored field value (4 FP32, 2 FP16/BF16)
     int pitch;  // elements per x row in device memory (nx rounded up to 16 bytes)
     int variant, tx, ty, tz;  // systolic tile shape
+    int cl;                   // CTAs per thread-block cluster along x (1, or 2: x pairs of tiles)
     int gx, gy, gz;
     long long ntiles_max;
     int source_steps, steps_per_launch;
@@ -155,6 +156,7 @@ bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, const fdtd_boundary &
     L.ntiles_max = 0;
     L.variant = pick_variant(c);
     if (L.variant < 0) return false;
+    L.cl = c.scheme == FDTD_SCHEME_SYSTOLIC && c.cluster[0] == 2 ? 2 : 1;
     const SysShape sh = systolic_shape(L.variant);
     L.tx = sh.tx;
     L.ty = sh.ty;
@@ -201,8 +203,11 @@ fdtd_status check_args(const fdtd_grid *g, const fdtd_coeffs *c, const fdtd_boun
     // the shared-memory systolic kernels (tiles 31x15x15, 31x7x15) hold FP32 only
     if (c->scheme == FDTD_SCHEME_SYSTOLIC && c->storage != FDTD_STORAGE_F32 && pick_variant(*c) < 2)
         return FDTD_ERR_UNSUPPORTED;
-    for (int a = 0; a < 3; ++a)
-        if (c->cluster[a] > 1) return FDTD_ERR_UNSUPPORTED;
+    // clusters: one CTA, or x pairs {2,1,1} of the lossless 31 x 15 x 12
+    // register tile under the systolic scheme
+    if (c->cluster[1] > 1 || c->cluster[2] > 1 || c->cluster[0] > 2) return FDTD_ERR_UNSUPPORTED;
+    if (c->cluster[0] == 2 && (c->scheme != FDTD_SCHEME_SYSTOLIC || pick_variant(*c) != 2 || conducts(*b)))
+        return FDTD_ERR_UNSUPPORTED;
     if (b->kind < FDTD_BOUNDARY_PEC || b->kind > FDTD_BOUNDARY_LEARNED) return FDTD_ERR_INVALID_ARG;
     if (b->kind == FDTD_BOUNDARY_GRADED_ABSORBER && !b->model) {
         if (b->thickness < 1 || !(b->sigma_max >= 0.0) || !std::isfinite(b->sigma_max) || b->poly_order < 0 ||
@@ -266,24 +271,42 @@ void build_tiles(const fdtd_grid &g, const Layout &L, int order, unsigned seed,
                  std::vector<int> &tiles, std::vector<long long> &count_le)
 {
     const int T = L.steps_per_launch;
+    // x pairs: one entry per pair of tiles (I = 2P, 2P + 1), whose start is
+    // the upwind tile's (starts grow with I), id P + gxp * (J + gy * K); a
+    // pair's tiles depend on pairs (P-1, J, K), (P, J-1, K), (P, J, K-1) and
+    // on each other, so the same sort is a topological order of pairs
+    const int cl = L.cl, gxp = (L.gx + cl - 1) / cl;
+    auto interval = [&](int I, int J, int K, int &s, int &e) {
+        const int ax = I * L.tx, ay = J * L.ty, az = K * L.tz;
+        s = std::max(0, std::max(ax - g.nx + 1, std::max(ay - g.ny + 1, az - g.nz + 1)));
+        const int ge = std::min(ax + L.tx - 1, std::min(ay + L.ty - 1, az + L.tz - 1));
+        e = std::min(T - 1, ge);
+    };
     std::vector<TileEntry> v;
     v.reserve((size_t)std::min<long long>(L.ntiles_max, 1ll << 26));
     for (int K = 0; K < L.gz; ++K)
         for (int J = 0; J < L.gy; ++J)
-            for (int I = 0; I < L.gx; ++I) {
-                const int ax = I * L.tx, ay = J * L.ty, az = K * L.tz;
-                const int s = std::max(0, std::max(ax - g.nx + 1, std::max(ay - g.ny + 1, az - g.nz + 1)));
-                const int ge = std::min(ax + L.tx - 1, std::min(ay + L.ty - 1, az + L.tz - 1));
-                const int e = std::min(T - 1, ge);
-                if (s > e + 1) continue;
+            for (int Pp = 0; Pp < gxp; ++Pp) {
+                int s = 0, e = -1;
+                bool kept = false;
+                for (int r = 0; r < cl; ++r) {
+                    const int I = Pp * cl + r;
+                    if (I >= L.gx) continue;
+                    int si, ei;
+                    interval(I, J, K, si, ei);
+                    if (si > ei + 1) continue;
+                    if (!kept || si < s) s = si;
+                    kept = true;
+                }
+                if (!kept) continue;
                 TileEntry te;
                 te.start = s;
-                te.id = I + L.gx * (J + L.gy * K);
+                te.id = Pp + gxp * (J + L.gy * K);
                 if (order == 2) {
                     te.diag = K;
-                    te.key = (unsigned)(J * L.gx + I);
+                    te.key = (unsigned)(J * gxp + Pp);
                 } else {
-                    te.diag = I + J + K;
+                    te.diag = Pp + J + K;
                     unsigned h = (unsigned)te.id * 2654435761u ^ seed;
                     h ^= h >> 15;
                     h *= 2246822519u;
@@ -648,15 +671,21 @@ fdtd_status fdtd_create(const fdtd_grid *grid, const double *eps, const fdtd_coe
     if (e != cudaSuccess) return fail(cuda_status(e));
 
     if (coeffs->scheme == FDTD_SCHEME_SYSTOLIC) {
-        e = systolic_configure(L.variant, h->fmt, h->ca != nullptr);
+        e = systolic_configure(L.variant, h->fmt, h->ca != nullptr, L.cl);
         if (e != cudaSuccess) return fail(cuda_status(e));
         int dev = 0, sms = 0;
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return fail(cuda_status(e));
-        const int per_sm = systolic_max_ctas_per_sm(L.variant, h->fmt, h->ca != nullptr);
-        if (per_sm < 1) return fail(FDTD_ERR_UNSUPPORTED);
-        h->max_ctas = sms * per_sm;
+        if (L.cl == 2) {  // co-resident clusters of two
+            const int pairs = systolic_reg_max_pairs(L.variant - 2, h->fmt);
+            if (pairs < 1) return fail(FDTD_ERR_UNSUPPORTED);
+            h->max_ctas = 2 * pairs;
+        } else {
+            const int per_sm = systolic_max_ctas_per_sm(L.variant, h->fmt, h->ca != nullptr);
+            if (per_sm < 1) return fail(FDTD_ERR_UNSUPPORTED);
+            h->max_ctas = sms * per_sm;
+        }
         if (L.variant >= 2) {
             const long long fstride = (long long)(L.fields[1] - L.fields[0]) / L.eb;
             const int nr = systolic_reg_rows(L.variant - 2);
@@ -828,8 +857,9 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         p.dbg_param2 = h->dbg_param2;
         p.src = h->src;
         if (h->L.variant >= 2) std::memcpy(p.tm, h->tm, sizeof(p.tm));
-        const int grid = (int)std::max<long long>(1, std::min<long long>(p.ntiles, h->max_ctas));
-        CK(launch_systolic(p, grid, h->stream, h->L.variant, h->fmt));
+        const int cl = h->L.cl;
+        const int grid = cl * (int)std::max<long long>(1, std::min<long long>(p.ntiles, h->max_ctas / cl));
+        CK(launch_systolic(p, grid, h->stream, h->L.variant, h->fmt, cl));
         h->launches += 1;
         h->epoch += (unsigned)T + 1u;
         h->step += T;

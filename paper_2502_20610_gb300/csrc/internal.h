@@ -64,8 +64,11 @@ struct SysShape { int tx, ty, tz; };
 constexpr int SYS_NSHAPES = 4;  // 2, 3: register-resident kernel, 31 x 15 x 12 / x 8 (systolic_reg.cu)
 SysShape systolic_shape(int variant);
 SysShape systolic_reg_shape(int k);
-cudaError_t systolic_reg_configure(int k, int fmt, bool lossy);
+// cl: CTAs per thread-block cluster along x (1, or 2 for x pairs of the
+// 31 x 15 x 12 lossless tile)
+cudaError_t systolic_reg_configure(int k, int fmt, bool lossy, int cl);
 int systolic_reg_max_ctas_per_sm(int k, int fmt, bool lossy);
+int systolic_reg_max_pairs(int k, int fmt);  // co-resident x-pair clusters, 0 if unsupported
 
 struct SysLaunch {
     float *f[6];             // field arrays (elements of the storage format; FP32 for the
@@ -126,11 +129,13 @@ size_t systolic_smem_bytes(int variant);
 // `fmt` is a kernel format code as for the naive scheme; the shared-memory
 // variants (0, 1) take FP32 only.
 // Lossy (absorber) launches need the register kernel (variant >= 2).
-cudaError_t systolic_configure(int variant, int fmt, bool lossy);
+cudaError_t systolic_configure(int variant, int fmt, bool lossy, int cl = 1);
 int systolic_max_ctas_per_sm(int variant, int fmt, bool lossy);
-cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant, int fmt);
-cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int fmt);
+// `grid` CTAs; with cl = 2 a multiple of 2 (one cluster per x pair of tiles)
+cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int variant, int fmt, int cl = 1);
+cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int fmt, int cl);
 
-// Tile order for one systolic launch of up to T steps (fdtd_api.cu).
+// Tile order for one systolic launch of up to T steps (fdtd_api.cu), single
+// tiles (clusters of one).
 void systolic_tile_order(const fdtd_grid &g, int variant, int T, std::vector<int> &tiles,
                          std::vector<long long> &count_le, int &gx, int &gy, int &gz);

@@ -405,10 +405,10 @@ SysShape systolic_shape(int v) { return v >= 2 ? systolic_reg_shape(v - 2) : kSh
 
 size_t systolic_smem_bytes(int v) { return v == 0 ? RingA::smem_bytes() : RingB::smem_bytes(); }
 
-cudaError_t systolic_configure(int v, int storage, bool lossy)
+cudaError_t systolic_configure(int v, int storage, bool lossy, int cl)
 {
-    if (v >= 2) return systolic_reg_configure(v - 2, storage, lossy);
-    if (storage != FDTD_STORAGE_F32 || lossy) return cudaErrorInvalidValue;
+    if (v >= 2) return systolic_reg_configure(v - 2, storage, lossy, cl);
+    if (storage != FDTD_STORAGE_F32 || lossy || cl != 1) return cudaErrorInvalidValue;
     if (v == 0)
         return cudaFuncSetAttribute(systolic_kernel<RingA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)RingA::smem_bytes());
@@ -428,10 +428,10 @@ int systolic_max_ctas_per_sm(int v, int storage, bool lossy)
     return e == cudaSuccess ? n : 0;
 }
 
-cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int v, int storage)
+cudaError_t launch_systolic(const SysLaunch &p, int grid, cudaStream_t st, int v, int storage, int cl)
 {
-    if (v >= 2) return launch_systolic_reg(p, grid, st, v - 2, storage);
-    if (storage != FDTD_STORAGE_F32 || p.ca) return cudaErrorInvalidValue;
+    if (v >= 2) return launch_systolic_reg(p, grid, st, v - 2, storage, cl);
+    if (storage != FDTD_STORAGE_F32 || p.ca || cl != 1) return cudaErrorInvalidValue;
     if (v == 0)
         systolic_kernel<RingA><<<grid, RingA::NTHREADS, RingA::smem_bytes(), st>>>(p);
     else

@@ -78,10 +78,14 @@ namespace {
 
 using namespace sysc;
 
-template <int NZ_, class S_, bool LOSSY_, int TY_>
+template <int NZ_, class S_, bool LOSSY_, int TY_, int CL_ = 1>
 struct RegTile {
     using S = S_;
     static constexpr bool LOSSY = LOSSY_;  // conducting cells: E <- ca E + cb curl H
+    // CTAs per thread-block cluster along x: 2 = pairs of x-adjacent tiles,
+    // the upwind one sending its top x face through distributed shared memory
+    static constexpr int CL = CL_;
+    static_assert(CL_ == 1 || (CL_ == 2 && !LOSSY_), "clusters of one, or x pairs of lossless tiles");
     using T = typename S_::T;
     static constexpr int NZ = NZ_;        // updated z rows (registers 0..NZ-1)
     static constexpr int NR = NZ_ + 1;    // plus the shell row -1
@@ -131,9 +135,14 @@ struct RegTile {
     // step) unless the lossy form's second coefficient set leaves no room
     static constexpr int NBUF = LOSSY_ ? 1 : 2;
     static constexpr size_t STG_B = OFF_XC + r128(NCOEF * 4 * (size_t)XBC);  // one buffer, bytes
+    // x pairs: the downwind tile's receive ring of x faces, NSLOT slots of
+    // [field][box row y][z-block] (rows 1..NZ of the x shell of one step)
+    static constexpr int NSLOT = 6;
+    static constexpr int RXS = 6 * 16 * BZ;  // elements per slot
+    static constexpr size_t RX_B = CL_ == 2 ? NSLOT * (size_t)RXS * EB : 0;
     static constexpr size_t smem_bytes()
     {
-        return NBUF * STG_B + sizeof(float) * (4 * (size_t)XE_F + NCOEF * (size_t)CE_F);
+        return NBUF * STG_B + sizeof(float) * (4 * (size_t)XE_F + NCOEF * (size_t)CE_F) + RX_B;
     }
 };
 
@@ -219,6 +228,83 @@ __device__ __forceinline__ void tma_box5(void *dst, const CUtensorMap *map, int 
                  : "memory");
 }
 
+// Thread-block cluster primitives (x pairs).
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// the shared::cluster address of local shared address `a` in CTA `rank`
+__device__ __forceinline__ unsigned mapa(unsigned a, unsigned rank)
+{
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+// every thread of every CTA of the cluster (orders all prior memory accesses,
+// distributed shared memory included, before all later ones)
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void st_remote_u32(unsigned a, unsigned v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void arrive_remote(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Four rows of one field into another CTA's shared memory (16 bytes FP32,
+// 8 bytes 16-bit, packed as st4 does).
+template <class S>
+__device__ __forceinline__ void st4_remote(unsigned a, float is, float x, float y, float z, float w)
+{
+    if constexpr (sizeof(typename S::T) == 4) {
+        asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z), "f"(w)
+                     : "memory");
+    } else {
+        asm volatile("st.shared::cluster.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(S::enc2(x, y, is)),
+                     "r"(S::enc2(z, w, is))
+                     : "memory");
+    }
+}
+template <class S, int NR>
+__device__ __forceinline__ void st_rows_remote(unsigned a, float is, const float (&v)[NR])
+{
+#pragma unroll
+    for (int q = 0; q < (NR - 1) / 4; ++q)
+        st4_remote<S>(a + 4 * q * (unsigned)sizeof(typename S::T), is, v[4 * q + 1], v[4 * q + 2], v[4 * q + 3],
+                      v[4 * q + 4]);
+}
+
+// Bounded wait (acquire at cluster scope) for phase `parity` of a local
+// mbarrier that a partner CTA of the cluster completes.  Returns false (error
+// word set) past the launch's timeout.
+__device__ bool wait_cluster_bar(const SysLaunch &P, unsigned long long *bar, unsigned parity, int ticket)
+{
+    unsigned long long t0 = 0;
+    for (int it = 0;; ++it) {
+        unsigned done;
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;"
+                     " selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (done) return true;
+        if (ld_volatile(P.ctrl + 1) != DEV_OK) return false;
+        const unsigned long long now = globaltimer();
+        if (it == 0) {
+            t0 = now;
+        } else if (now - t0 > (unsigned long long)P.timeout_ns) {
+            if (atomicCAS(P.ctrl + 1, DEV_OK, DEV_ERR_TIMEOUT) == DEV_OK) {
+                P.ctrl[2] = ticket;
+                P.ctrl[3] = -2;
+            }
+            return false;
+        }
+    }
+}
+
 // Bounded wait for phase `parity` of the staging barrier.  Returns false if
 // the wait ran past the launch's timeout (the error word is then set).
 __device__ bool wait_stage(const SysLaunch &P, unsigned long long *bar, unsigned parity, int ticket)
@@ -264,7 +350,12 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     // stays in place while the skewed register rows move past it
     float *const CEs = XHz + R::XE_F;      // [warp][physical z mod CR][lane]
     float *const CAs = CEs + R::CE_F;      // the same for ca (lossy only)
+    // x pairs: the receive ring of x faces (downwind CTA), after the rings
+    T *const RX = reinterpret_cast<T *>(CEs + R::NCOEF * R::CE_F);  // [slot][field][box row][BZ]
     __shared__ int s_ticket, s_abort;
+    // x pairs: a slot of the receive ring is full (the upwind CTA arrives
+    // once its x lanes have written it) / free again (the downwind CTA arrives)
+    __shared__ alignas(8) unsigned long long s_rxf[R::NSLOT], s_rxe[R::NSLOT];
     __shared__ alignas(8) unsigned long long s_bar[2];  // staging barriers, one per buffer: one phase per fill
     // state of the next step's shells, decided during this one: 0 = the
     // upwind tiles have not published them yet, 1 = published and fetched
@@ -321,9 +412,31 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
         s_niss[0] = s_niss[1] = 0u;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[0])) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[1])) : "memory");
+        if constexpr (R::CL == 2) {
+#pragma unroll
+            for (int k = 0; k < R::NSLOT; ++k) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_rxf[k])) : "memory");
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_rxe[k])) : "memory");
+            }
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // x pairs: rank 0 holds the upwind tile (I even), rank 1 the downwind one;
+    // every CTA of the cluster must be running before distributed shared
+    // memory is touched
+    const unsigned rank = R::CL == 2 ? cluster_rank() : 0u;
+    if constexpr (R::CL == 2) cluster_sync_all();
+    const unsigned rx_remote = R::CL == 2 ? mapa(smem_u32(RX), 1u) : 0u;        // rank 0 -> rank 1's ring
+    const unsigned rxf_remote = R::CL == 2 ? mapa(smem_u32(&s_rxf[0]), 1u) : 0u;
+    const unsigned rxe_remote = R::CL == 2 ? mapa(smem_u32(&s_rxe[0]), 0u) : 0u;  // rank 1 -> rank 0
+    // messages (x faces) sent / received over this CTA's life: message m
+    // uses slot m % NSLOT, its (m / NSLOT)-th use of that slot
+    int msg_base = 0;
+    // slot to signal after the next block barrier (the y-shell warp does it):
+    // rank 0, the slot its x lanes have just filled; rank 1, the slot its x
+    // lane has just read
+    int sig_slot = -1;
     // fills waited for on each buffer (every thread waits on every fill, so
     // every thread keeps the same counts)
     unsigned n_wait0 = 0, n_wait1 = 0;
@@ -353,19 +466,64 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     float ex[NR], ey[NR], ez[NR], hx[NR], hy[NR], hz[NR];
 
     for (;;) {
-        if (tid == 0) {
-            s_ticket = atomicAdd(P.ctrl, 1);
-            s_abort = ld_volatile(P.ctrl + 1) != DEV_OK;
-            s_pref = 0;
+        if constexpr (R::CL == 2) {
+            // the pair takes one ticket: both CTAs have finished their previous
+            // tiles (barrier), rank 0 takes the ticket and reads the error
+            // word for both, both read them after the second barrier, so the
+            // two always stop together
+            cluster_sync_all();
+            if (rank == 0 && tid == 0) {
+                const int tk = atomicAdd(P.ctrl, 1);
+                const int ab = ld_volatile(P.ctrl + 1) != DEV_OK;
+                s_ticket = tk;
+                s_abort = ab;
+                st_remote_u32(mapa(smem_u32(&s_ticket), 1u), (unsigned)tk);
+                st_remote_u32(mapa(smem_u32(&s_abort), 1u), (unsigned)ab);
+            }
+            if (tid == 0) s_pref = 0;
+            if (tid < 3) s_seen[tid] = 0u;
+            cluster_sync_all();
+        } else {
+            if (tid == 0) {
+                s_ticket = atomicAdd(P.ctrl, 1);
+                s_abort = ld_volatile(P.ctrl + 1) != DEV_OK;
+                s_pref = 0;
+            }
+            if (tid < 3) s_seen[tid] = 0u;
+            __syncthreads();
         }
-        if (tid < 3) s_seen[tid] = 0u;
-        __syncthreads();
         const int ticket = s_ticket;
         const bool stop = s_abort || ticket >= P.ntiles;
         __syncthreads();
         if (stop) break;
-        const int tile = P.tiles[ticket];
-        const int I = tile % P.gx, J = (tile / P.gx) % P.gy, K = tile / (P.gx * P.gy);
+        bool abort = false;
+        int nmsg = 0;
+        do {  // one tile (`break` leaves it early: an abort, or a pair member without a tile)
+        int I, J, K;
+        int m_lo = 1, m_hi = 0;  // x pairs: steps whose x face goes through the ring
+        if constexpr (R::CL == 2) {
+            const int gxp = (P.gx + 1) / 2, pr = P.tiles[ticket];
+            const int pp = pr % gxp;
+            J = (pr / gxp) % P.gy;
+            K = pr / (gxp * P.gy);
+            I = 2 * pp + (int)rank;
+            if (2 * pp + 1 < P.gx) {
+                const Interval i0 = tile_interval<TX, TY, TZ>(P, 2 * pp, J, K);
+                const Interval i1 = tile_interval<TX, TY, TZ>(P, 2 * pp + 1, J, K);
+                if (i0.s <= i0.e && i1.s <= i1.e) {
+                    m_lo = i1.s;
+                    m_hi = min(i0.e, i1.e);
+                }
+            }
+            nmsg = max(0, m_hi - m_lo + 1);
+            if (I >= P.gx) break;  // the last pair of an odd tile row has one tile
+        } else {
+            const int tl = P.tiles[ticket];
+            I = tl % P.gx;
+            J = (tl / P.gx) % P.gy;
+            K = tl / (P.gx * P.gy);
+        }
+        const int tile = I + P.gx * (J + P.gy * K);
         const int Ax = I * TX, Ay = J * TY, Az = K * TZ;
         const int kb = K % P.nzblk;  // this tile's z-block in the face buffers
         T *const XFk = XF + (long long)kb * P.nx * P.ny * BZ;
@@ -380,7 +538,7 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 if (tid == 0) s_abort = !ok;
             }
             __syncthreads();
-            if (s_abort) break;
+            if (s_abort) { abort = true; break; }
         }
         if (iv.s > iv.e) {  // enters the domain only after this launch: relay only
             if (tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.s);
@@ -431,7 +589,6 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
         }
         if (iv.s > 0 && tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.s);
 
-        bool abort = false;
         // may a point source lie in the box during this tile's steps?  (per
         // axis, the box holds coordinate c at steps A - c .. A - c + n - 1)
         bool tile_src = false;
@@ -479,6 +636,22 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             }
             __syncthreads();  // B1
             if (s_abort) { abort = true; break; }
+            // x pairs: this step's x face travels through ring slot `slot`
+            const bool msg = R::CL == 2 && t >= m_lo && t <= m_hi;
+            const bool rx_msg = msg && rank == 1, tx_msg = msg && rank == 0;
+            const int mi = msg_base + (t - m_lo);
+            const int slot = mi % R::NSLOT;
+            if constexpr (R::CL == 2) {
+                // every lane is past last step's ring accesses: rank 0's x
+                // lanes have written the slot (the release covers their stores),
+                // rank 1's x lane has read it; the y-shell warp, idle in the H
+                // half-step, tells the partner
+                if (sig_slot >= 0) {
+                    if (w == ((by - 1) & (R::RY - 1)) && lane == 0)
+                        arrive_remote((rank == 0 ? rxf_remote : rxe_remote) + 8u * (unsigned)sig_slot);
+                    sig_slot = -1;
+                }
+            }
             // unless the previous step found this step's shells published,
             // wait here for the upwind tiles' level t; fetch the shells now
             // unless they were fetched during the previous step
@@ -603,10 +776,17 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 CEs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZSC[oc];
                 if (R::LOSSY) CAs[(w * CR + ((bz - 1) & (CR - 1))) * 32 + lane] = ZSA[oc];
                 if (!xbox) {  // the lane leaving the tile in x: rows 1..NZ of H from the x-face shell
+                    // (x pairs: from the ring, once the upwind CTA's lanes have arrived)
                     const T *xs = XST + (dy + 1) * BZ;
-                    ld_rows<S>(xs + 3 * R::XB, SC(3), hx);
-                    ld_rows<S>(xs + 4 * R::XB, SC(4), hy);
-                    ld_rows<S>(xs + 5 * R::XB, SC(5), hz);
+                    int xst = R::XB;
+                    if (R::CL == 2 && rx_msg) {
+                        if (!wait_cluster_bar(P, &s_rxf[slot], (unsigned)(mi / R::NSLOT) & 1u, ticket)) s_abort = 1;
+                        xs = RX + slot * R::RXS + dy * BZ;
+                        xst = 16 * BZ;
+                    }
+                    ld_rows<S>(xs + 3 * xst, SC(3), hx);
+                    ld_rows<S>(xs + 4 * xst, SC(4), hy);
+                    ld_rows<S>(xs + 5 * xst, SC(5), hz);
                     CLEAR_OUT_ROWS(hx, hy, hz);
                     const float *xsc = XSC + dy * R::XAC + xec;
                     const float *xsa = XSA + dy * R::XAC + xec;
@@ -714,11 +894,13 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     ey[0] = S::dec(ZST[1 * R::ZB + o], SC(1));
                     ez[0] = S::dec(ZST[2 * R::ZB + o], SC(2));
                 }
-                if (!xbox) {  // the x lane: rows 1..NZ of E from the x-face shell
-                    const T *xs = XST + (dy + 1) * BZ;
+                if (!xbox) {  // the x lane: rows 1..NZ of E from the x-face shell (or the ring)
+                    const bool ring = R::CL == 2 && rx_msg;
+                    const T *xs = ring ? RX + slot * R::RXS + dy * BZ : XST + (dy + 1) * BZ;
+                    const int xst = ring ? 16 * BZ : R::XB;
                     ld_rows<S>(xs, SC(0), ex);
-                    ld_rows<S>(xs + R::XB, SC(1), ey);
-                    ld_rows<S>(xs + 2 * R::XB, SC(2), ez);
+                    ld_rows<S>(xs + xst, SC(1), ey);
+                    ld_rows<S>(xs + 2 * xst, SC(2), ez);
                     CLEAR_OUT_ROWS(ex, ey, ez);
                 }
             }
@@ -768,14 +950,40 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 }
             }
             // top x face (all rows of the lane leaving the box in x) into the
-            // x-face buffer, where the downwind tile's x shell is fetched
-            if (ybox && dx == TX - 1 && (unsigned)px < (unsigned)P.nx && (unsigned)py < (unsigned)P.ny)
-                FACE_STORE(XFk + ((long long)px * P.ny + py) * BZ, P.fxs, bz);
+            // x-face buffer, where the downwind tile's x shell is fetched.
+            // x pairs, rank 0: into rank 1's ring instead (its slot was freed
+            // before the second barrier), every box row's lane then arriving
+            // on the slot's barrier; the top box row still goes to the x-face
+            // buffer too (the corner of the next pair's y shell)
+            if (ybox && dx == TX - 1) {
+                if (R::CL == 2 && tx_msg) {
+                    // the slot's previous message must have been read
+                    if (mi >= R::NSLOT &&
+                        !wait_cluster_bar(P, &s_rxe[slot], (unsigned)((mi / R::NSLOT) - 1) & 1u, ticket))
+                        s_abort = 1;
+                    const unsigned a = rx_remote + (unsigned)((slot * R::RXS + dy * BZ) * (int)sizeof(T));
+                    constexpr unsigned FS = 16u * BZ * (unsigned)sizeof(T);
+                    st_rows_remote<S>(a, IS(0), ex);
+                    st_rows_remote<S>(a + FS, IS(1), ey);
+                    st_rows_remote<S>(a + 2 * FS, IS(2), ez);
+                    st_rows_remote<S>(a + 3 * FS, IS(3), hx);
+                    st_rows_remote<S>(a + 4 * FS, IS(4), hy);
+                    st_rows_remote<S>(a + 5 * FS, IS(5), hz);
+                }
+                if ((!(R::CL == 2 && tx_msg) || dy == TY - 1) && (unsigned)px < (unsigned)P.nx &&
+                    (unsigned)py < (unsigned)P.ny)
+                    FACE_STORE(XFk + ((long long)px * P.ny + py) * BZ, P.fxs, bz);
+            }
+            if (R::CL == 2 && msg) sig_slot = slot;
         }
         if (abort) break;
         // the last step's top y face (the launch's last one included: the
         // downwind tile reads it from the y-face buffer), then its progress
         __syncthreads();
+        if (R::CL == 2 && sig_slot >= 0) {  // the tile's last message: filled / read
+            if (tid == 0) arrive_remote((rank == 0 ? rxf_remote : rxe_remote) + 8u * (unsigned)sig_slot);
+            sig_slot = -1;
+        }
         {
             const int pbx = Ax - iv.e, pby = Ay - iv.e, pbz = Az - iv.e;
             const int pdx = (lane - pbx) & 31, pdy = (w - pby) & (R::RY - 1);
@@ -785,6 +993,10 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
         }
         __syncthreads();
         if (tid == 0) publish(P, tile, ticket, P.epoch + (unsigned)iv.e + 1u);
+        } while (false);
+        msg_base += nmsg;
+        sig_slot = -1;
+        if (R::CL == 1 && abort) break;  // a pair leaves together, at the next ticket
     }
     // after an abort, bulk copies may still be writing into the staging
     // buffers: wait for them (bounded) before the CTA's shared memory goes
@@ -792,6 +1004,9 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
         while (n_wait0 < s_niss[0] && wait_stage(P, &s_bar[0], n_wait0 & 1u, -1)) ++n_wait0;
         while (n_wait1 < s_niss[1] && wait_stage(P, &s_bar[1], n_wait1 & 1u, -1)) ++n_wait1;
     }
+    // x pairs: neither CTA leaves while its partner may still write into its
+    // shared memory
+    if constexpr (R::CL == 2) cluster_sync_all();
 }
 
 #undef F0
@@ -818,10 +1033,15 @@ constexpr int REG_TY = 15;
 template <int NZ>
 struct RegShape {
     static constexpr bool HAS_LOSSY = NZ == 12;
-    static cudaError_t configure(int fmt, bool lossy)
+    static constexpr bool HAS_PAIRS = NZ == 12;  // x pairs in thread-block clusters: the 31 x 15 x 12 tile
+    static cudaError_t configure(int fmt, bool lossy, int cl)
     {
         if (lossy) {
-            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S, true, REG_TY>>());
+            if constexpr (HAS_LOSSY) if (cl == 1) DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S, true, REG_TY>>());
+            return cudaErrorInvalidValue;
+        }
+        if (cl == 2) {
+            if constexpr (HAS_PAIRS) DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S, false, REG_TY, 2>>());
             return cudaErrorInvalidValue;
         }
         DISPATCH_FORMAT(fmt, S, set<RegTile<NZ, S, false, REG_TY>>());
@@ -834,10 +1054,19 @@ struct RegShape {
         }
         DISPATCH_FORMAT(fmt, S, occ<RegTile<NZ, S, false, REG_TY>>());
     }
-    static cudaError_t launch(const SysLaunch &p, int grid, cudaStream_t st, int fmt)
+    static int clusters(int fmt)
+    {
+        if constexpr (HAS_PAIRS) DISPATCH_FORMAT(fmt, S, occ_pairs<RegTile<NZ, S, false, REG_TY, 2>>());
+        return 0;
+    }
+    static cudaError_t launch(const SysLaunch &p, int grid, cudaStream_t st, int fmt, int cl)
     {
         if (p.ca) {
-            if constexpr (HAS_LOSSY) DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S, true, REG_TY>>(p, grid, st));
+            if constexpr (HAS_LOSSY) if (cl == 1) DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S, true, REG_TY>>(p, grid, st));
+            return cudaErrorInvalidValue;
+        }
+        if (cl == 2) {
+            if constexpr (HAS_PAIRS) DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S, false, REG_TY, 2>>(p, grid, st));
             return cudaErrorInvalidValue;
         }
         DISPATCH_FORMAT(fmt, S, go<RegTile<NZ, S, false, REG_TY>>(p, grid, st));
@@ -858,10 +1087,41 @@ struct RegShape {
                    : 0;
     }
     template <class R>
+    static cudaLaunchConfig_t config(int grid, cudaStream_t st, cudaLaunchAttribute *at)
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3((unsigned)R::NT);
+        cfg.dynamicSmemBytes = R::smem_bytes();
+        cfg.stream = st;
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)R::CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cfg;
+    }
+    // co-resident clusters of a pair kernel on this device
+    template <class R>
+    static int occ_pairs()
+    {
+        cudaLaunchAttribute at[1];
+        cudaLaunchConfig_t cfg = config<R>(2, 0, at);
+        int n = 0;
+        return cudaOccupancyMaxActiveClusters(&n, systolic_reg_kernel<R>, &cfg) == cudaSuccess ? n : 0;
+    }
+    template <class R>
     static cudaError_t go(const SysLaunch &p, int grid, cudaStream_t st)
     {
-        systolic_reg_kernel<R><<<grid, R::NT, R::smem_bytes(), st>>>(p);
-        return cudaGetLastError();
+        if constexpr (R::CL == 1) {
+            systolic_reg_kernel<R><<<grid, R::NT, R::smem_bytes(), st>>>(p);
+            return cudaGetLastError();
+        } else {
+            cudaLaunchAttribute at[1];
+            cudaLaunchConfig_t cfg = config<R>(grid, st, at);
+            return cudaLaunchKernelEx(&cfg, systolic_reg_kernel<R>, p);
+        }
     }
 };
 
@@ -874,9 +1134,9 @@ int systolic_reg_rows(int k) { return (k == 0 ? 12 : 8) + 1; }
 
 SysShape systolic_reg_shape(int k) { return SysShape{31, REG_TY, k == 0 ? 12 : 8}; }
 
-cudaError_t systolic_reg_configure(int k, int fmt, bool lossy)
+cudaError_t systolic_reg_configure(int k, int fmt, bool lossy, int cl)
 {
-    return k == 0 ? RegA::configure(fmt, lossy) : RegB::configure(fmt, lossy);
+    return k == 0 ? RegA::configure(fmt, lossy, cl) : RegB::configure(fmt, lossy, cl);
 }
 
 int systolic_reg_max_ctas_per_sm(int k, int fmt, bool lossy)
@@ -884,7 +1144,9 @@ int systolic_reg_max_ctas_per_sm(int k, int fmt, bool lossy)
     return k == 0 ? RegA::per_sm(fmt, lossy) : RegB::per_sm(fmt, lossy);
 }
 
-cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int fmt)
+int systolic_reg_max_pairs(int k, int fmt) { return k == 0 ? RegA::clusters(fmt) : RegB::clusters(fmt); }
+
+cudaError_t launch_systolic_reg(const SysLaunch &p, int grid, cudaStream_t st, int k, int fmt, int cl)
 {
-    return k == 0 ? RegA::launch(p, grid, st, fmt) : RegB::launch(p, grid, st, fmt);
+    return k == 0 ? RegA::launch(p, grid, st, fmt, cl) : RegB::launch(p, grid, st, fmt, cl);
 }

@@ -143,8 +143,11 @@ TILES = {"31x15x15": (31, 15, 15), "31x7x15": (31, 7, 15), "31x15x12": (31, 15, 
 
 def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
                 steps_per_launch=0, max_source_steps=0, boundary="pec", tile=None, field_scale=None,
-                absorber=None, learned=None):
-    """absorber: (thickness L, sigma_max, order m) of the graded layer when
+                absorber=None, learned=None, cluster=None):
+    """cluster: CTAs per thread-block cluster (x, y, z) of the systolic
+    scheme: None or (1, 1, 1), or (2, 1, 1) for x pairs of tiles exchanging
+    their common face through distributed shared memory.
+    absorber: (thickness L, sigma_max, order m) of the graded layer when
     boundary == "graded", or a float64 array of per-cell conductivity (kept
     alive by the caller); learned: (thickness, params[, sigma_max, order])
     when boundary == "learned" (params: float32 numpy array, kept alive by
@@ -164,6 +167,9 @@ def make_params(shape_zyx, dt, scheme="systolic", storage="f32", timeout_s=2.0,
         t = TILES[tile] if isinstance(tile, str) else tuple(tile)
         for a in range(3):
             c.tile[a] = int(t[a])
+    if cluster is not None:
+        for a in range(3):
+            c.cluster[a] = int(cluster[a])
     b = Boundary()
     b.kind = BOUNDARY[boundary]
     if isinstance(absorber, np.ndarray):
@@ -215,7 +221,7 @@ class Sim:
 
     def __init__(self, shape_zyx, eps, dt, scheme="systolic", device=None, timeout_s=2.0,
                  steps_per_launch=0, max_source_steps=0, tile=None, storage="f32", field_scale=None,
-                 boundary="pec", absorber=None, learned=None):
+                 boundary="pec", absorber=None, learned=None, cluster=None):
         import torch
         self._lib = load_library()
         self.shape = tuple(int(s) for s in shape_zyx)
@@ -229,7 +235,7 @@ class Sim:
         g, c, b = make_params(self.shape, dt, scheme=scheme, timeout_s=timeout_s,
                               steps_per_launch=steps_per_launch, max_source_steps=max_source_steps,
                               tile=tile, storage=storage, field_scale=field_scale, boundary=boundary,
-                              absorber=absorber, learned=self._learned_args(learned))
+                              absorber=absorber, learned=self._learned_args(learned), cluster=cluster)
         self._params = (g, c, b)
         n = ctypes.c_size_t(0)
         _check(self._lib.fdtd_workspace_size(ctypes.byref(g), ctypes.byref(c), ctypes.byref(b),
