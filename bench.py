@@ -499,7 +499,26 @@ def run_config4(device, stream, measure):
     e_p, _ = learned.reflection(setup, "pec", seed=99, steps=300, ref_fields=trace)
     del trace
     torch.cuda.empty_cache()
+    # the same comparison on config 4's own grid: the yardstick is 384^3 with
+    # the 32-cell absorber (320^3 interior); the other domains are that
+    # interior plus a 4-cell layer (328^3); a Gaussian-modulated Jz pulse
+    # (wavelength 20) at a seeded position, every domain stepped together
+    big = learned.Setup(n=328, thickness=4, pad=28, absorber=(32, 0.5, 3), base_sigma=0.3)
+    bsteps = 700
+    u = wl.uniform_pm1(4242, 3)
+    pos = [int(40 + 248 * (0.5 + 0.5 * float(v))) for v in u]  # 40 .. 288 in each axis
+    bsrc = (2, pos[0], pos[1], pos[2], wl.gaussian_pulse_source(bsteps, wl.DT_DEFAULT, wavelength=WAVELENGTH))
+    t_big = time.time()
+    big_err = learned.reflection_lockstep(big, {
+        "learned_4cell": ("learned", nets[2][0], None), "base_layer_alone": ("thin", None, None),
+        "graded_4cell_sigma0.5": ("thin", None, 0.5), "pec": ("pec", None, None)}, bsrc, bsteps)
+    t_big = time.time() - t_big
+    torch.cuda.empty_cache()
     out = {"config": "config4", "record_seconds": t_record, "train_pairs": 1000000,
+           "reflection_384cube": {"errors": big_err, "steps": bsteps, "source_xyz": pos,
+                                  "network": "training seeds (shuffle 0, init 1)",
+                                  "domain": "yardstick 384^3 with the 32-cell absorber; 328^3 = its 320^3 "
+                                            "interior + 4-cell layer; eps 2.1", "seconds": t_big},
            "trainings": [{"shuffle_seed": sd, "init_seed": ini, "train_seconds": ts, "train_loss": ls,
                           "reflection": e} for (_, ls, ts, sd, ini), e in zip(nets, e_ls)],
            "reflection_error_vs_32cell_absorber": {"learned_4cell_mean": float(np.mean(e_ls)),

@@ -22,7 +22,8 @@
 // passes, column sums for the bias gradients, and Adam.  The layer update of
 // a simulation step is one fused persistent kernel: it gathers the stencils
 // of 64 layer cells into shared memory and runs the three layers on them
-// with the weights resident in shared memory.
+// with the weights resident in shared memory, the two large contractions on
+// the tensor cores (mma.sync TF32, three-term split for FP32 accuracy).
 #include "internal.h"
 #include "mlp.h"
 #include "yee_cell.cuh"
@@ -378,10 +379,78 @@ __global__ void __launch_bounds__(256) record_kernel(const float *__restrict__ p
 
 // -------------------------------------------------- layer update (fused)
 
+// Tensor-core contraction of the fused layer kernel: mma.sync m16n8k8 with
+// TF32 operands and FP32 accumulation, each operand split in two TF32 terms
+// (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)) and the product taken as
+// lo*hi + hi*lo + hi*hi ("3xTF32"): ~22 significant bits per operand, the
+// dropped lo*lo term below FP32 rounding of the sum, so the layer keeps
+// FP32 accuracy.
+__device__ __forceinline__ unsigned tf32_rna(float x)
+{
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo)
+{
+    hi = tf32_rna(x);
+    lo = tf32_rna(__fsub_rn(x, __uint_as_float(hi)));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                         unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9},"
+                 " {%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Shared tiles [k][64] (k = input feature or unit, 64 = cells or units) are
+// stored with the column index XOR-swizzled by (k mod 4) * 8, so the
+// fragment loads of a warp (rows k .. k+3, eight consecutive columns each)
+// hit 32 different banks.
+__device__ __forceinline__ int swz(int k, int c) { return c ^ ((k & 3) << 3); }
+
+// D[64 x 64] of this CTA's eight warps (warp w: rows 16*(w%4).., columns
+// 32*(w/4).., four m16n8 tiles) = sum_k A[k][row] B[k][col] over K (a
+// multiple of 8; A, B swizzled [k][64] tiles in shared memory).
+template <int K>
+__device__ __forceinline__ void warp_gemm_3xtf32(const float *A, const float *B, float (&acc)[4][4])
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int m0 = 16 * (w & 3), n0 = 32 * (w >> 2);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+#pragma unroll 2
+    for (int k0 = 0; k0 < K; k0 += 8) {
+        const int ka = k0 + q, kb = k0 + q + 4;
+        unsigned ah[4], al[4];
+        split_tf32(A[ka * 64 + swz(ka, m0 + g)], ah[0], al[0]);
+        split_tf32(A[ka * 64 + swz(ka, m0 + g + 8)], ah[1], al[1]);
+        split_tf32(A[kb * 64 + swz(kb, m0 + g)], ah[2], al[2]);
+        split_tf32(A[kb * 64 + swz(kb, m0 + g + 8)], ah[3], al[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + 8 * j + g;
+            unsigned bh0, bl0, bh1, bl1;
+            split_tf32(B[ka * 64 + swz(ka, n)], bh0, bl0);
+            split_tf32(B[kb * 64 + swz(kb, n)], bh1, bl1);
+            mma_tf32(acc[j], al[0], al[1], al[2], al[3], bh0, bh1);
+            mma_tf32(acc[j], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+            mma_tf32(acc[j], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+        }
+    }
+}
+
 // Shared memory of the fused layer kernel, in floats; the float4-read arrays
 // come first, each a multiple of 64 floats, so they stay 16-byte aligned.
 constexpr int LC = 64;  // layer cells per tile
-constexpr int SM_W1T = NI * NH, SM_W2T = NH * NH, SM_W3T = NH * NO, SM_XT = NI * LC, SM_H = NH * LC;
+constexpr int NIP = 328;  // NI padded to a multiple of 8 (zero rows)
+static_assert((NIP - NI) * LC == 256, "one padding float per thread of the layer kernel");
+constexpr int SM_W1T = NIP * NH, SM_W2T = NH * NH, SM_W3T = NH * NO, SM_XT = NIP * LC, SM_H = NH * LC;
 constexpr size_t LAYER_SMEM =
     sizeof(float) * (SM_W1T + SM_W2T + SM_XT + 2 * SM_H + SM_W3T + 2 * NH + NO + 2 * LC + 4 * LC);
 
@@ -404,11 +473,12 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
     const int tid = threadIdx.x;
     for (int e = tid; e < NH * NI; e += 256) {
         const int u = e / NI, k = e - u * NI;
-        W1t[k * NH + u] = P[OFF_W1 + e];
+        W1t[k * NH + swz(k, u)] = P[OFF_W1 + e];
     }
+    for (int e = tid; e < (NIP - NI) * NH; e += 256) W1t[NI * NH + e] = 0.f;  // padding rows
     for (int e = tid; e < NH * NH; e += 256) {
         const int u = e / NH, k = e - u * NH;
-        W2t[k * NH + u] = P[OFF_W2 + e];
+        W2t[k * NH + swz(k, u)] = P[OFF_W2 + e];
     }
     for (int e = tid; e < NO * NH; e += 256) {
         const int o = e / NH, k = e - o * NH;
@@ -420,7 +490,6 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
     }
     if (tid < NO) b3[tid] = P[OFF_B3 + tid];
     const long long sxy = (long long)pitch * ny;
-    const int tm = tid >> 4, tn = tid & 15;
     const int ntiles = (ncells + LC - 1) / LC;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();  // previous tile done with Xt / H / rr
@@ -440,13 +509,13 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
                 for (int pq = 0; pq < 3; ++pq) {
                     const int pr = p0 + pq, lev = pr / 6, comp = pr - lev * 6;
                     const float *src = (lev == 0 ? cur : prev) + comp * fstride + centre;
-                    float *dst = Xt + (pr * 27) * LC + q;
 #pragma unroll
                     for (int d = 0; d < 27; ++d) {
                         const int dx = d % 3, dy = (d / 3) % 3, dz = d / 9;
+                        const int k = pr * 27 + d;
                         float v = 0.f;
                         if (vx[dx] && vy[dy] && vz[dz]) v = src[(dx - 1) + (long long)pitch * (dy - 1) + sxy * (dz - 1)];
-                        dst[d * LC] = v;
+                        Xt[k * LC + swz(k, q)] = v;
                         ss = __fmaf_rn(v, v, ss);
                     }
                 }
@@ -454,8 +523,12 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
 #pragma unroll
                 for (int pq = 0; pq < 3; ++pq)
 #pragma unroll
-                    for (int d = 0; d < 27; ++d) Xt[((p0 + pq) * 27 + d) * LC + q] = 0.f;
+                    for (int d = 0; d < 27; ++d) {
+                        const int k = (p0 + pq) * 27 + d;
+                        Xt[k * LC + swz(k, q)] = 0.f;
+                    }
             }
+            Xt[NI * LC + tid] = 0.f;  // padding rows of the stencil (256 zeros)
             part[(tid >> 6) * LC + q] = ss;
         }
         __syncthreads();
@@ -467,46 +540,30 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
             ir[tid] = live ? 1.f / r : 0.f;
         }
         __syncthreads();
-        // layer 1: H1 = tanh((W1 x) / r + b1), cells tm*4.., units tn*4..
-        // (unrolled so the shared loads of later k are issued ahead)
+        // layers 1 and 2 on the tensor cores (3xTF32): H1 = tanh((W1 x) / r +
+        // b1), H2 = tanh(W2 H1 + b2); warp w holds cells 16*(w%4) + g (+8) and
+        // units 32*(w/4) + 8j + 2q (+1) of its accumulator fragments
         {
-            float acc[4][4] = {};
-#pragma unroll 6
-            for (int k = 0; k < NI; ++k) {
-                const float4 a = *reinterpret_cast<const float4 *>(Xt + k * LC + tm * 4);
-                const float4 w = *reinterpret_cast<const float4 *>(W1t + k * NH + tn * 4);
-                const float av[4] = {a.x, a.y, a.z, a.w}, wv[4] = {w.x, w.y, w.z, w.w};
+            const int lane = tid & 31, w = tid >> 5, g = lane >> 2, q = lane & 3;
+            const int m0 = 16 * (w & 3), n0 = 32 * (w >> 2);
+            float acc[4][4];
+            warp_gemm_3xtf32<NIP>(Xt, W1t, acc);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = __fmaf_rn(av[i], wv[j], acc[i][j]);
-            }
+                for (int e = 0; e < 4; ++e) {
+                    const int cell = m0 + g + 8 * (e >> 1), unit = n0 + 8 * j + 2 * q + (e & 1);
+                    H1t[unit * LC + swz(unit, cell)] = tanhf(__fmaf_rn(acc[j][e], ir[cell], b1[unit]));
+                }
+            __syncthreads();
+            warp_gemm_3xtf32<NH>(H1t, W2t, acc);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    H1t[(tn * 4 + j) * LC + tm * 4 + i] =
-                        tanhf(__fmaf_rn(acc[i][j], ir[tm * 4 + i], b1[tn * 4 + j]));
-        }
-        __syncthreads();
-        // layer 2
-        {
-            float acc[4][4] = {};
-#pragma unroll 8
-            for (int k = 0; k < NH; ++k) {
-                const float4 a = *reinterpret_cast<const float4 *>(H1t + k * LC + tm * 4);
-                const float4 w = *reinterpret_cast<const float4 *>(W2t + k * NH + tn * 4);
-                const float av[4] = {a.x, a.y, a.z, a.w}, wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = __fmaf_rn(av[i], wv[j], acc[i][j]);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    H2t[(tn * 4 + j) * LC + tm * 4 + i] = tanhf(__fadd_rn(acc[i][j], b2[tn * 4 + j]));
+                for (int e = 0; e < 4; ++e) {
+                    const int cell = m0 + g + 8 * (e >> 1), unit = n0 + 8 * j + 2 * q + (e & 1);
+                    H2t[unit * LC + swz(unit, cell)] = tanhf(__fadd_rn(acc[j][e], b2[unit]));
+                }
         }
         __syncthreads();
         // layer 3: the correction r f added to the Yee step later
@@ -515,7 +572,7 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
             const int cell = tile * LC + q;
             if (cell >= ncells) continue;
             float f = b3[o];
-            for (int k = 0; k < NH; ++k) f = __fmaf_rn(H2t[k * LC + q], W3t[k * NO + o], f);
+            for (int k = 0; k < NH; ++k) f = __fmaf_rn(H2t[k * LC + swz(k, q)], W3t[k * NO + o], f);
             const unsigned m = tangent_mask(cells[3 * cell], cells[3 * cell + 1], cells[3 * cell + 2], nx, ny, nz);
             out[(long long)cell * NO + o] = (m >> o) & 1u ? __fmul_rn(rr[q], f) : 0.f;
         }

@@ -175,3 +175,40 @@ def reflection(setup, kind, params=None, seed=99, steps=400, ref_fields=None, si
         den += float((ref_fields[s] ** 2).sum())
     sim.close()
     return num / den, ref_fields
+
+
+def reflection_lockstep(setup, boundaries, source, steps):
+    """Reflection errors of several boundaries at once against the thick
+    absorber (the yardstick), stepping every domain together so that no
+    trace of the reference is stored (for large grids).
+
+    boundaries: {name: (kind, params, sigma)} for setup.sim; source: (comp,
+    x, y, z, J) in D coordinates.  Returns {name: error}: the energy of
+    (field - yardstick's field) in D's interior summed over `steps` steps,
+    relative to the yardstick's energy there (FP64 sums on the device)."""
+    import torch
+    t = setup.thickness
+    inner = slice(t, setup.n - t)
+    p0, p1 = setup.pad + t, setup.pad + setup.n - t
+    c, x, y, z, J = source
+    ref = setup.ref_sim(scheme="naive", max_source_steps=steps, with_layer=False)
+    ref.add_source(c, x + setup.pad, y + setup.pad, z + setup.pad, J)
+    sims = {}
+    for name, (kind, params, sigma) in boundaries.items():
+        s = setup.sim(kind, params, max_source_steps=steps, sigma=sigma)
+        s.add_source(c, x, y, z, J)
+        sims[name] = s
+    num = {name: torch.zeros((), dtype=torch.float64, device=ref.device) for name in sims}
+    den = torch.zeros((), dtype=torch.float64, device=ref.device)
+    for _ in range(steps):
+        ref.step(1)
+        r = ref.read_fields()[:, p0:p1, p0:p1, p0:p1]
+        den += (r.double() ** 2).sum()
+        for name, s in sims.items():
+            s.step(1)
+            f = s.read_fields()[:, inner, inner, inner]
+            num[name] += ((f.double() - r.double()) ** 2).sum()
+    ref.close()
+    for s in sims.values():
+        s.close()
+    return {name: float(num[name] / den) for name in sims}
