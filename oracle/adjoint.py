@@ -140,3 +140,22 @@ def yee_step(E, H, c, dt, M):
     H = H - dt * curl_f(E)
     E = E + M * c[None] * curl_b(H)
     return E, H
+
+
+def objective_window(shape, eps, fields0, steps, sources, obj, dt, quantize=False):
+    """The objective L of `forward`, computed without keeping the E history:
+    the oracle steps straight to the window, then reads Ez step by step (for
+    finite differences on grids whose history would not fit in memory)."""
+    o = YeeOracle(shape, dt, eps, quantize_ce_f32=quantize)
+    o.set_fields(fields0)
+    for (c, i, j, k, J) in sources:
+        o.add_source(c, i, j, k, J)
+    first = max(1, steps - obj.window + 1)
+    if first > 1:
+        o.step(first - 1)
+    L = 0.0
+    for n in range(first, steps + 1):
+        o.step(1)
+        L += obj.weight(n, steps) * obj.overlap(o.fields()[:3]) ** 2
+    o.close()
+    return L

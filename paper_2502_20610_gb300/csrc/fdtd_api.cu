@@ -463,6 +463,15 @@ struct fdtd_sim {
     std::vector<double> eps_host;
     long long step;
     unsigned epoch;
+    // adjoint: systolic launches store the E of box [cap_lo, cap_hi) after
+    // each step into plane (step + 1 - cap_s0) of cap (3*cap_bc floats per
+    // plane), `step` the step count before that step.  The recompute sets
+    // cap_s0 to the segment's first step (plane 0 holds that state, copied
+    // separately); the window sets it one past the chunk's first step, so
+    // plane 0 holds the state after the chunk's first step.
+    float *cap = nullptr;
+    int cap_lo[3] = {0, 0, 0}, cap_hi[3] = {0, 0, 0};
+    long long cap_bc = 0, cap_s0 = 0;
     long long launches;
     int max_ctas;
     std::vector<long long> count_le;  // tiles with start <= s
@@ -856,6 +865,12 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
         p.dbg_param = h->dbg_param;
         p.dbg_param2 = h->dbg_param2;
         p.src = h->src;
+        p.cap = h->cap && h->L.variant >= 2 ? h->cap + 3 * h->cap_bc * (h->step + 1 - h->cap_s0) : nullptr;
+        for (int a = 0; a < 3; ++a) {
+            p.cap_lo[a] = h->cap_lo[a];
+            p.cap_hi[a] = h->cap_hi[a];
+        }
+        p.cap_bc = h->cap_bc;
         if (h->L.variant >= 2) std::memcpy(p.tm, h->tm, sizeof(p.tm));
         const int cl = h->L.cl;
         const int grid = cl * (int)std::max<long long>(1, std::min<long long>(p.ntiles, h->max_ctas / cl));
@@ -1056,8 +1071,11 @@ namespace {
 
 struct AdjPlan {
     long long nseg, box_cells, arr;  // arr: floats of one field array (stride)
-    size_t ck, lam, hist, ov, total;
+    size_t ck, lam, hist, ov, win, total;
 };
+
+// planes of the objective's window captured per systolic launch
+constexpr int64_t ADJ_WINDOW_CHUNK = 128;
 
 bool adj_plan(fdtd_handle h, int64_t n, int32_t K, const int32_t lo[3], const int32_t hi[3], AdjPlan &a)
 {
@@ -1070,12 +1088,16 @@ bool adj_plan(fdtd_handle h, int64_t n, int32_t K, const int32_t lo[3], const in
     size_t off = 0;
     a.ck = off;  // checkpoints 0 .. nseg-1 and the final state
     off = align_up(off + sizeof(float) * 6 * (size_t)a.arr * (size_t)(a.nseg + 1));
-    a.lam = off;
-    off = align_up(off + sizeof(float) * 6 * (size_t)a.arr);
+    a.lam = off;  // two adjoint states (the fused step reads one, writes the other)
+    off = align_up(off + sizeof(float) * 12 * (size_t)a.arr);
     a.hist = off;
     off = align_up(off + sizeof(float) * 3 * (size_t)a.box_cells * (size_t)(K + 1));
     a.ov = off;
     off = align_up(off + sizeof(double) * (size_t)(n + 1));
+    // the objective's window as captured planes (E of plane k0 after each of
+    // the last `window` steps), for handles whose register kernel captures
+    a.win = off;
+    off = align_up(off + sizeof(float) * 3 * (size_t)h->g.nx * h->g.ny * (size_t)std::min<int64_t>(n, ADJ_WINDOW_CHUNK));
     a.total = off;
     return true;
 }
@@ -1109,6 +1131,7 @@ fdtd_status fdtd_adjoint_gradient(fdtd_handle h, const fdtd_overlap_objective *o
     const long long N = n_steps, W = obj->window;
     char *base = (char *)d_scratch;
     float *ck = (float *)(base + a.ck), *lam = (float *)(base + a.lam), *hist = (float *)(base + a.hist);
+    float *lam2 = lam + 6 * (size_t)a.arr;
     double *ov = (double *)(base + a.ov);
     float *f0 = (float *)h->f[0];
     const size_t state_bytes = sizeof(float) * 6 * (size_t)a.arr;
@@ -1119,8 +1142,10 @@ fdtd_status fdtd_adjoint_gradient(fdtd_handle h, const fdtd_overlap_objective *o
     cudaStream_t st = h->stream;
     const float dt = (float)h->c.dt;
     fdtd_status rs;
-    // single steps (window, recompute) use the naive kernel pair, which the
-    // systolic schedule reproduces bit for bit
+    // single steps (the objective's window; the recompute unless the
+    // register kernel can capture the box) use the naive kernel pair, which
+    // the systolic schedule reproduces bit for bit
+    const bool reg_kernel = h->c.scheme == FDTD_SCHEME_SYSTOLIC && h->L.variant >= 2;
     auto one_step = [&]() -> cudaError_t {
         cudaError_t e = launch_naive_h(h->f, h->fmt, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, -dt, h->sc, st);
         if (e == cudaSuccess)
@@ -1134,6 +1159,8 @@ fdtd_status fdtd_adjoint_gradient(fdtd_handle h, const fdtd_overlap_objective *o
     // forward: checkpoints every K steps, the overlaps of the window's steps
     CK(cudaMemsetAsync(ov, 0, sizeof(double) * (size_t)(N + 1), st));
     CK(cudaMemsetAsync(d_grad, 0, sizeof(double) * (size_t)a.box_cells, st));
+    float *win = (float *)(base + a.win);
+    const long long plane = (long long)h->g.nx * h->g.ny;
     long long n = 0;
     while (n < N) {
         if (n % K == 0) CK(cudaMemcpyAsync(slot(n / K), f0, state_bytes, cudaMemcpyDeviceToDevice, st));
@@ -1144,9 +1171,31 @@ fdtd_status fdtd_adjoint_gradient(fdtd_handle h, const fdtd_overlap_objective *o
             n = upto;
             continue;
         }
+        if (n < N - W) {  // up to the window's first step
+            if ((rs = fdtd_step(h, N - W - n)) != FDTD_OK) return rs;
+            n = N - W;
+            continue;
+        }
+        if (reg_kernel) {  // window steps in systolic launches that capture plane k0
+            const long long m = std::min(upto, n + ADJ_WINDOW_CHUNK) - n;
+            h->cap = win;  // plane w = the state after step n + 1 + w
+            h->cap_s0 = h->step + 1;
+            h->cap_bc = plane;
+            h->cap_lo[0] = h->cap_lo[1] = 0;
+            h->cap_hi[0] = h->g.nx;
+            h->cap_hi[1] = h->g.ny;
+            h->cap_lo[2] = obj->k0;
+            h->cap_hi[2] = obj->k0 + 1;
+            rs = fdtd_step(h, m);
+            h->cap = nullptr;
+            if (rs != FDTD_OK) return rs;
+            CK(adjoint_overlaps(win, plane, (int)m, obj->d_mode, ov + n + 1, st));
+            n += m;
+            continue;
+        }
         CK(one_step());
         ++n;
-        if (n > N - W) CK(adjoint_overlap(g, f0 + 2 * a.arr, obj->k0, obj->d_mode, ov + n, st));
+        CK(adjoint_overlap(g, f0 + 2 * a.arr, obj->k0, obj->d_mode, ov + n, st));
     }
     CK(cudaMemcpyAsync(slot(a.nseg), f0, state_bytes, cudaMemcpyDeviceToDevice, st));
     std::vector<double> O((size_t)(N + 1));
@@ -1168,16 +1217,30 @@ fdtd_status fdtd_adjoint_gradient(fdtd_handle h, const fdtd_overlap_objective *o
         CK(cudaMemcpyAsync(f0, slot(s), state_bytes, cudaMemcpyDeviceToDevice, st));
         h->step = step0 + s0;
         CK(adjoint_box_copy(g, f0, lo, hi, hist, st));
-        for (long long q = s0 + 1; q <= s1; ++q) {
-            CK(one_step());
-            CK(adjoint_box_copy(g, f0, lo, hi, hist + 3 * (size_t)bc * (size_t)(q - s0), st));
+        if (reg_kernel) {  // the segment in systolic launches that store the box's E of every step
+            h->cap = hist;
+            h->cap_s0 = h->step;
+            h->cap_bc = bc;
+            for (int q = 0; q < 3; ++q) {
+                h->cap_lo[q] = lo[q];
+                h->cap_hi[q] = hi[q];
+            }
+            rs = fdtd_step(h, s1 - s0);
+            h->cap = nullptr;
+            if (rs != FDTD_OK) return rs;
+        } else {
+            for (long long q = s0 + 1; q <= s1; ++q) {
+                CK(one_step());
+                CK(adjoint_box_copy(g, f0, lo, hi, hist + 3 * (size_t)bc * (size_t)(q - s0), st));
+            }
         }
         for (long long q = s1 - 1; q >= s0; --q) {
-            // lambda holds lambda^{q+1}: gradient, then lambda^q
-            CK(adjoint_h(g, lam, h->ce, lo, hi, hist + 3 * (size_t)bc * (size_t)(q + 1 - s0),
-                         hist + 3 * (size_t)bc * (size_t)(q - s0), dt, d_grad, st));
-            CK(adjoint_e(g, lam, dt, obj->k0, obj->d_mode, amp(q), st));
-            h->launches += 2;
+            // lambda^{q+1} -> gradient and lambda^q, one fused kernel
+            CK(adjoint_step(g, lam, lam2, h->ce, lo, hi, hist + 3 * (size_t)bc * (size_t)(q + 1 - s0),
+                            hist + 3 * (size_t)bc * (size_t)(q - s0), dt, d_grad, obj->k0, obj->d_mode, amp(q),
+                            st));
+            std::swap(lam, lam2);
+            h->launches += 1;
         }
     }
     // leave the simulation at step n_steps

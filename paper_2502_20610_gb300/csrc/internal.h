@@ -102,6 +102,12 @@ struct SysLaunch {
     int dbg_kind;
     long long dbg_ticket, dbg_param, dbg_param2;
     SrcSet src;
+    // register kernel, optional: the E of the cells of box [cap_lo, cap_hi)
+    // after every step t of the launch into cap + 3*cap_bc*t (component a at
+    // + a*cap_bc, box cells x fastest), for the adjoint's recompute; null = off
+    float *cap;
+    int cap_lo[3], cap_hi[3];
+    long long cap_bc;
     // bulk-tensor (TMA) maps of the register kernel's shell staging:
     // [shell][0] the six fields, [shell][1] the FP32 coefficients cb (dt/eps)
     // and, when lossy, ca, each with the array index as a 4th dimension;

@@ -138,6 +138,8 @@ extern "C" fdtd_status fdtd_systolic_step_noalloc(const fdtd_grid *grid, float *
     p.xf = p.yf = nullptr;  // the shared-memory kernel keeps its faces in the field arrays
     p.fxs = p.fys = 0;
     p.nzb = p.nzblk = 0;
+    p.cap = nullptr;
+    p.cap_bc = 0;
     p.gx = gx;
     p.gy = gy;
     p.gz = gz;

@@ -931,6 +931,25 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 }
             }
 
+            // the adjoint's recompute: this step's E of the cells of the
+            // capture box (tiles that meet it only)
+            if (P.cap && colin && bx < P.cap_hi[0] && bx + TX > P.cap_lo[0] && by < P.cap_hi[1] &&
+                by + TY > P.cap_lo[1] && bz < P.cap_hi[2] && bz + TZ > P.cap_lo[2] && px >= P.cap_lo[0] &&
+                px < P.cap_hi[0] && py >= P.cap_lo[1] && py < P.cap_hi[1]) {
+                float *cp = P.cap + 3 * P.cap_bc * (long long)t;
+                const int cbx = P.cap_hi[0] - P.cap_lo[0], cby = P.cap_hi[1] - P.cap_lo[1];
+                const long long cxy = (long long)(px - P.cap_lo[0]) + (long long)cbx * (py - P.cap_lo[1]);
+#pragma unroll
+                for (int i = 1; i < NR; ++i) {
+                    const int z = bz + i - 1;
+                    if (z >= P.cap_lo[2] && z < P.cap_hi[2]) {
+                        const long long b = cxy + (long long)cbx * cby * (z - P.cap_lo[2]);
+                        cp[b] = ex[i];
+                        cp[P.cap_bc + b] = ey[i];
+                        cp[2 * P.cap_bc + b] = ez[i];
+                    }
+                }
+            }
             // G. stores: the whole box on the launch's last step, else the top faces
             if (t == P.T - 1) {
                 if (colin) {

@@ -98,3 +98,41 @@ def test_autograd_and_finite_differences(cuda_device):
         worst = max(worst, abs(got - fd) / scale)
         assert abs(got - fd) <= 1e-3 * scale, (q, got, fd)
     print(f"16 voxels: largest |adjoint - central difference| / scale = {worst:.2e}")
+
+
+def test_midsize_gradient_16_voxels_central_differences(cuda_device):
+    """A mid-size problem (64 x 64 x 48 cells, 1000 steps, checkpoints every
+    100, a 16 x 16 x 8 design box): the GPU gradient on 16 seeded random
+    voxels of the box against central differences of the FP64 oracle's
+    objective (eps perturbed by 1e-5 relative, in FP64)."""
+    nz, ny, nx = 48, 64, 64
+    steps = 1000
+    lo, hi = (24, 24, 16), (40, 40, 24)       # x, y, z
+    bg = np.full((nz, ny, nx), 2.1)
+    u = np.asarray(wl.uniform_pm1(31, 16 * 16 * 8), np.float64).reshape(8, 16, 16)
+    eps_box = 2.1 + 10.0 * (0.5 + 0.5 * u)
+    mode = np.asarray(wl.uniform_pm1(32, ny * nx)).reshape(ny, nx)
+    src = (2, 32, 32, 10, wl.sine_source(steps, DT, 20.0))
+    p = gadj.Problem((nz, ny, nx), bg, lo, hi, src, k0=32, mode=mode, n_steps=steps, window=150,
+                     checkpoint_every=100, scheme="systolic")
+    L, g = p.run(eps_box)
+    g = g.cpu().numpy()
+    obj = adj.Objective(p.k0, p.mode.numpy().astype(np.float64), p.window)
+    c, i, j, k, J = p.source
+    f0 = np.zeros((6, nz, ny, nx))
+    Lo = adj.objective_window(p.shape, p.eps_with(eps_box), f0, steps, [(c, i, j, k, J)], obj, DT, quantize=True)
+    assert abs(L - Lo) <= 1e-4 * Lo, (L, Lo)
+    order = np.argsort(wl.splitmix64(33, 0, eps_box.size))
+    worst = 0.0
+    for v in order[:16]:
+        q = tuple(int(t) for t in np.unravel_index(int(v), eps_box.shape))
+        h = 1e-5 * eps_box[q]
+        ep, em = eps_box.copy(), eps_box.copy()
+        ep[q] += h
+        em[q] -= h
+        fd = (adj.objective_window(p.shape, p.eps_with(ep), f0, steps, [(c, i, j, k, J)], obj, DT) -
+              adj.objective_window(p.shape, p.eps_with(em), f0, steps, [(c, i, j, k, J)], obj, DT)) / (2 * h)
+        scale = max(abs(fd), 1e-2 * float(np.abs(g).max()))
+        worst = max(worst, abs(g[q] - fd) / scale)
+        assert abs(g[q] - fd) <= 1e-3 * scale, (q, g[q], fd)
+    print(f"mid-size, 16 voxels: largest |adjoint - central difference| / scale = {worst:.2e}")

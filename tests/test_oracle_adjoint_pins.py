@@ -65,3 +65,17 @@ def test_gradient_matches_central_differences():
         em[k, j, i] -= h
         fd = (adj.objective(shape, ep, f0, steps, src, obj, DT) - adj.objective(shape, em, f0, steps, src, obj, DT)) / (2 * h)
         assert abs(fd - g[k, j, i]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(g).max()), ((k, j, i), fd, g[k, j, i])
+
+
+def test_windowed_objective_equals_the_history_objective():
+    # the no-history form used for finite differences on larger grids
+    shape = (9, 10, 11)
+    eps = wl.random_eps(shape, 6, lo=2.1, hi=12.1)
+    steps = 40
+    src = [(1, 5, 4, 3, wl.sine_source(steps, DT, 9.0))]
+    mode = np.asarray(wl.uniform_pm1(7, 10 * 11)).reshape(10, 11)
+    obj = adj.Objective(k0=6, mode=mode, window=13)
+    f0 = np.zeros((6,) + shape)
+    a = adj.objective(shape, eps, f0, steps, src, obj, DT)
+    b = adj.objective_window(shape, eps, f0, steps, src, obj, DT)
+    assert a > 0 and abs(a - b) <= 1e-14 * a
