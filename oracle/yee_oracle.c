@@ -193,6 +193,8 @@ static void round_field(yee_oracle *o, int c)
     if (o->sp <= 0) return;
     long n = ncell(o);
     double s = o->sscale[c];
+    /* every element is rounded on its own: threads do not change the result */
+#pragma omp parallel for schedule(static)
     for (long q = 0; q < n; ++q) o->f[c][q] = s * oracle_round_to_format(o->f[c][q] / s, o->sp, o->semin, o->semax);
 }
 
