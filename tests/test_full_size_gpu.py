@@ -6,11 +6,11 @@ times (one persistent launch per call of 2000 steps, default tile).
   minute on 16 cores): per-field relative L2 <= 1e-4 on every field (Sec. 2,
   Eq. 1 in FP64 against the same operations in FP32).
 * The 1024^3 grid is too large for the oracle to follow over many steps;
-  there the checks are properties that hold at any size: the systolic
-  result equals the naive one bit for bit, and the discrete energy of a
-  source-free PEC box, Q = sum eps |E^n|^2 + sum H^{n-1/2} . H^{n+1/2}
-  (computed here in FP64 with plain torch ops), is conserved to FP32
-  round-off.
+  there the check is a property that holds at any size: the systolic
+  result equals the naive one bit for bit.  At 256^3 a second property is
+  checked over 2000 steps: the discrete energy of a source-free PEC box,
+  Q = sum eps |E^n|^2 + sum H^{n-1/2} . H^{n+1/2} (computed here in FP64
+  with plain torch ops), is conserved to FP32 round-off.
 """
 import numpy as np
 import pytest
