@@ -311,8 +311,9 @@ typedef struct {
 } fdtd_overlap_objective;
 
 /* Scratch of fdtd_adjoint_gradient: ceil(n_steps/checkpoint_every) + 1 field
- * states, the adjoint state, checkpoint_every + 1 E states of the box, and
- * n_steps + 1 doubles.  Errors: INVALID_ARG (box outside the grid). */
+ * states, the adjoint state, two histories of checkpoint_every + 1 E states
+ * of the box (forward and adjoint), n_steps + 1 doubles and up to 128 E
+ * states of the plane k0.  Errors: INVALID_ARG (box outside the grid). */
 fdtd_status fdtd_adjoint_scratch_size(fdtd_handle h, int64_t n_steps, int32_t checkpoint_every,
                                       const int32_t box_lo[3], const int32_t box_hi[3], size_t *bytes);
 
@@ -321,7 +322,10 @@ fdtd_status fdtd_adjoint_scratch_size(fdtd_handle h, int64_t n_steps, int32_t ch
  * [box_lo, box_hi) (x y z) in d_grad (device doubles, box cells x fastest).
  * The forward pass keeps a checkpoint every checkpoint_every steps; the
  * reverse sweep recomputes each segment from its checkpoint (keeping only
- * the box's E) and steps the adjoint back over it.  On return h holds the
+ * the box's E) and steps the adjoint back over it.  The adjoint state is
+ * kept as (M c lambda_E, -dt lambda_H), in which the transposed step is
+ * the forward Yee step, so both sweeps run on h's own scheme (the systolic
+ * kernel, when h has it).  On return h holds the
  * state after n_steps.  FP32 storage and PEC walls only (UNSUPPORTED
  * otherwise).  Synchronous.  Errors: INVALID_ARG, UNSUPPORTED, OOM (scratch
  * too small), TIMEOUT, CUDA, STATE. */

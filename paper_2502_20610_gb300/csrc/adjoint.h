@@ -9,18 +9,17 @@ struct AdjGeo {
     long long fstride;
 };
 
-// lambda (6 components, E then H): lambda_H += curl_f(M c lambda_E), and the
-// gradient of the box [lo, hi) from lambda_E and the box's E at steps n+1
-// (e_next) and n (e_now), [3][box cells], FP64 into grad [box cells].
-cudaError_t adjoint_h(const AdjGeo &g, float *lam, const float *ce, const int lo[3], const int hi[3],
-                      const float *e_next, const float *e_now, float dt, double *grad, cudaStream_t st);
-// lambda_E -= dt curl_b lambda_H, plus amp2 * mode(i,j) on Ez of plane k0.
-cudaError_t adjoint_e(const AdjGeo &g, float *lam, float dt, int k0, const float *mode, double amp2, cudaStream_t st);
-// Both of the above in one kernel (same FP32 results): the adjoint state
-// (6 components, E then H) from lam_old into lam_new.
-cudaError_t adjoint_step(const AdjGeo &g, const float *lam_old, float *lam_new, const float *ce, const int lo[3],
-                         const int hi[3], const float *e_next, const float *e_now, float dt, double *grad, int k0,
-                         const float *mode, double amp2, cudaStream_t st);
+// The objective's source in the adjoint's transformed variables
+// (Et = M c lambda_E): ez(i,j,k0) += M c(i,j,k0) amp2 mode(i,j), where ez is
+// the Ez component of a state in the workspace layout.
+cudaError_t adjoint_plane_source(const AdjGeo &g, float *ez, const float *ce, int k0, const float *mode, double amp2,
+                                 cudaStream_t st);
+// grad[b] -= (1/dt) sum_a Et_a^{q+1}(b) (E^{q+1} - E^q)_a(b) over the steps q
+// of a segment of `len` steps, last step first: e_hist planes 0..len hold the
+// box's E from the segment's first step on, et_hist planes 0..len-1 its Et
+// from the segment's last step back ([plane][3][box cells], x fastest).
+cudaError_t adjoint_gradient(const float *et_hist, const float *e_hist, long long box_cells, int len, double dt,
+                             double *grad, cudaStream_t st);
 // out[w] = sum m(i,j) Ez_w(i,j) for n captured planes [w][3][plane cells]
 // (component 2 = Ez), each in the same fixed order as adjoint_overlap
 cudaError_t adjoint_overlaps(const float *planes, long long plane_cells, int n, const float *mode, double *out,

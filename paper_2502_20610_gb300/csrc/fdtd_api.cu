@@ -1071,7 +1071,7 @@ namespace {
 
 struct AdjPlan {
     long long nseg, box_cells, arr;  // arr: floats of one field array (stride)
-    size_t ck, lam, hist, ov, win, total;
+    size_t ck, lam, hist, ahist, ov, win, total;
 };
 
 // planes of the objective's window captured per systolic launch
@@ -1088,9 +1088,11 @@ bool adj_plan(fdtd_handle h, int64_t n, int32_t K, const int32_t lo[3], const in
     size_t off = 0;
     a.ck = off;  // checkpoints 0 .. nseg-1 and the final state
     off = align_up(off + sizeof(float) * 6 * (size_t)a.arr * (size_t)(a.nseg + 1));
-    a.lam = off;  // two adjoint states (the fused step reads one, writes the other)
-    off = align_up(off + sizeof(float) * 12 * (size_t)a.arr);
-    a.hist = off;
+    a.lam = off;  // the adjoint state (transformed variables, the field layout)
+    off = align_up(off + sizeof(float) * 6 * (size_t)a.arr);
+    a.hist = off;  // the box's E over one segment
+    off = align_up(off + sizeof(float) * 3 * (size_t)a.box_cells * (size_t)(K + 1));
+    a.ahist = off;  // the box's adjoint Et over one segment
     off = align_up(off + sizeof(float) * 3 * (size_t)a.box_cells * (size_t)(K + 1));
     a.ov = off;
     off = align_up(off + sizeof(double) * (size_t)(n + 1));
@@ -1130,21 +1132,21 @@ fdtd_status fdtd_adjoint_gradient(fdtd_handle h, const fdtd_overlap_objective *o
     const int K = checkpoint_every;
     const long long N = n_steps, W = obj->window;
     char *base = (char *)d_scratch;
-    float *ck = (float *)(base + a.ck), *lam = (float *)(base + a.lam), *hist = (float *)(base + a.hist);
-    float *lam2 = lam + 6 * (size_t)a.arr;
+    float *ck = (float *)(base + a.ck), *lam = (float *)(base + a.lam);
+    float *hist = (float *)(base + a.hist), *ahist = (float *)(base + a.ahist);
     double *ov = (double *)(base + a.ov);
     float *f0 = (float *)h->f[0];
     const size_t state_bytes = sizeof(float) * 6 * (size_t)a.arr;
     auto slot = [&](long long s) { return ck + 6 * (size_t)a.arr * (size_t)s; };
     AdjGeo g{h->g.nx, h->g.ny, h->g.nz, h->L.pitch, a.arr};
     const int lo[3] = {box_lo[0], box_lo[1], box_lo[2]}, hi[3] = {box_hi[0], box_hi[1], box_hi[2]};
-    const long long step0 = h->step;
+    const long long step0 = h->step, bc = a.box_cells;
     cudaStream_t st = h->stream;
     const float dt = (float)h->c.dt;
     fdtd_status rs;
-    // single steps (the objective's window; the recompute unless the
-    // register kernel can capture the box) use the naive kernel pair, which
-    // the systolic schedule reproduces bit for bit
+    // single steps (the objective's window in the adjoint sweep, and every
+    // step unless the register kernel can capture the box) use the naive
+    // kernel pair, which the systolic schedule reproduces bit for bit
     const bool reg_kernel = h->c.scheme == FDTD_SCHEME_SYSTOLIC && h->L.variant >= 2;
     auto one_step = [&]() -> cudaError_t {
         cudaError_t e = launch_naive_h(h->f, h->fmt, h->g.nx, h->g.ny, h->g.nz, h->L.pitch, -dt, h->sc, st);
@@ -1154,6 +1156,27 @@ fdtd_status fdtd_adjoint_gradient(fdtd_handle h, const fdtd_overlap_objective *o
         h->launches += 2;
         h->step += 1;
         return e;
+    };
+    // m steps of h, the box's E after step r (r = 1..m) into plane p0 + r of
+    // buf: captured by the register kernel, or copied after single steps
+    auto run_capture = [&](long long m, float *buf, long long p0) -> fdtd_status {
+        if (reg_kernel) {
+            h->cap = buf;
+            h->cap_s0 = h->step - p0;
+            h->cap_bc = bc;
+            for (int q = 0; q < 3; ++q) {
+                h->cap_lo[q] = lo[q];
+                h->cap_hi[q] = hi[q];
+            }
+            const fdtd_status r = fdtd_step(h, m);
+            h->cap = nullptr;
+            return r;
+        }
+        for (long long r = 1; r <= m; ++r) {
+            CK(one_step());
+            CK(adjoint_box_copy(g, f0, lo, hi, buf + 3 * (size_t)bc * (size_t)(p0 + r), st));
+        }
+        return FDTD_OK;
     };
 
     // forward: checkpoints every K steps, the overlaps of the window's steps
@@ -1205,45 +1228,51 @@ fdtd_status fdtd_adjoint_gradient(fdtd_handle h, const fdtd_overlap_objective *o
     for (long long q = N - W + 1; q <= N; ++q) L += O[(size_t)q] * O[(size_t)q];
     if (loss) *loss = L;
 
-    // reverse sweep, segment by segment: recompute the box's E from the
-    // checkpoint, then step the adjoint back over the segment
-    CK(cudaMemsetAsync(lam, 0, state_bytes, st));
-    const long long bc = a.box_cells;
-    auto amp = [&](long long q) { return q > N - W ? 2.0 * O[(size_t)q] : 0.0; };
+    // reverse sweep, segment by segment from the last.  The adjoint state is
+    // kept as Et = M c lambda_E, Ht = -dt lambda_H, in which the transposed
+    // step is the forward Yee step (adjoint.cu), so it runs on h's own
+    // kernels with h's point sources switched off.  Per segment: recompute
+    // the box's E from the checkpoint, step the adjoint back over the
+    // segment keeping the box's Et, then accumulate the gradient.
+    auto amp = [&](long long q) { return 2.0 * O[(size_t)q]; };  // window steps q > N - W
+    struct SourcesOff {  // restores h's sources on every way out
+        fdtd_handle h;
+        SrcSet saved;
+        ~SourcesOff() { h->src = saved; }
+    } src_guard{h, h->src};
+    SrcSet no_src = h->src;
+    no_src.n = 0;
     // lambda^N = dg_N/dx^N: the adjoint source of step N alone
-    CK(adjoint_e(g, lam, 0.f, obj->k0, obj->d_mode, amp(N), st));
+    CK(cudaMemsetAsync(lam, 0, state_bytes, st));
+    CK(adjoint_plane_source(g, lam + 2 * a.arr, h->ce, obj->k0, obj->d_mode, amp(N), st));
     for (long long s = a.nseg - 1; s >= 0; --s) {
-        const long long s0 = s * K, s1 = std::min(N, s0 + K);
+        const long long s0 = s * K, s1 = std::min(N, s0 + K), len = s1 - s0;
+        // the box's E at steps s0 .. s1 into hist planes 0 .. len
+        h->src = src_guard.saved;
         CK(cudaMemcpyAsync(f0, slot(s), state_bytes, cudaMemcpyDeviceToDevice, st));
         h->step = step0 + s0;
         CK(adjoint_box_copy(g, f0, lo, hi, hist, st));
-        if (reg_kernel) {  // the segment in systolic launches that store the box's E of every step
-            h->cap = hist;
-            h->cap_s0 = h->step;
-            h->cap_bc = bc;
-            for (int q = 0; q < 3; ++q) {
-                h->cap_lo[q] = lo[q];
-                h->cap_hi[q] = hi[q];
-            }
-            rs = fdtd_step(h, s1 - s0);
-            h->cap = nullptr;
-            if (rs != FDTD_OK) return rs;
-        } else {
-            for (long long q = s0 + 1; q <= s1; ++q) {
-                CK(one_step());
-                CK(adjoint_box_copy(g, f0, lo, hi, hist + 3 * (size_t)bc * (size_t)(q - s0), st));
-            }
+        if ((rs = run_capture(len, hist, 0)) != FDTD_OK) return rs;
+        // the adjoint from lambda^{s1} down to lambda^{s0}: its step r goes
+        // from lambda^{q+1} to lambda^q, q = s1 - 1 - r, and adds the
+        // objective's source when q is in the window (those steps come
+        // first); the box's Et before step r into ahist plane r
+        h->src = no_src;
+        CK(cudaMemcpyAsync(f0, lam, state_bytes, cudaMemcpyDeviceToDevice, st));
+        CK(adjoint_box_copy(g, f0, lo, hi, ahist, st));
+        long long r = 0;
+        for (; r < len && s1 - 1 - r > N - W; ++r) {
+            CK(one_step());
+            CK(adjoint_plane_source(g, f0 + 2 * a.arr, h->ce, obj->k0, obj->d_mode, amp(s1 - 1 - r), st));
+            CK(adjoint_box_copy(g, f0, lo, hi, ahist + 3 * (size_t)bc * (size_t)(r + 1), st));
         }
-        for (long long q = s1 - 1; q >= s0; --q) {
-            // lambda^{q+1} -> gradient and lambda^q, one fused kernel
-            CK(adjoint_step(g, lam, lam2, h->ce, lo, hi, hist + 3 * (size_t)bc * (size_t)(q + 1 - s0),
-                            hist + 3 * (size_t)bc * (size_t)(q - s0), dt, d_grad, obj->k0, obj->d_mode, amp(q),
-                            st));
-            std::swap(lam, lam2);
-            h->launches += 1;
-        }
+        if (r < len && (rs = run_capture(len - r, ahist, r)) != FDTD_OK) return rs;
+        CK(cudaMemcpyAsync(lam, f0, state_bytes, cudaMemcpyDeviceToDevice, st));
+        CK(adjoint_gradient(ahist, hist, bc, (int)len, (double)dt, d_grad, st));
+        h->launches += 1;
     }
     // leave the simulation at step n_steps
+    h->src = src_guard.saved;
     CK(cudaMemcpyAsync(f0, slot(a.nseg), state_bytes, cudaMemcpyDeviceToDevice, st));
     h->step = step0 + N;
     return fdtd_sync(h);
