@@ -8,6 +8,9 @@
 * Central finite differences of the oracle's own objective on single
   voxels (including one next to the source and one on a wall), the
   independent definition of the gradient.
+* The identity the GPU's adjoint sweep rests on: in the variables
+  (M c lambda_E, -dt lambda_H) the transposed step is the forward step, and
+  the gradient computed that way equals the oracle's reverse sweep.
 """
 import numpy as np
 
@@ -79,3 +82,44 @@ def test_windowed_objective_equals_the_history_objective():
     a = adj.objective(shape, eps, f0, steps, src, obj, DT)
     b = adj.objective_window(shape, eps, f0, steps, src, obj, DT)
     assert a > 0 and abs(a - b) <= 1e-14 * a
+
+
+def test_transposed_step_is_the_forward_step_in_scaled_variables():
+    shape = (6, 7, 8)
+    rng = np.random.default_rng(4)
+    c = DT / wl.random_eps(shape, 5)
+    M = adj.pec_mask(shape)
+    le, lh = rng.standard_normal((3,) + shape), rng.standard_normal((3,) + shape)
+    te, th = adj.transposed_step(le, lh, c, DT, M)
+    fe, fh = adj.yee_step(M * c[None] * le, -DT * lh, c, DT, M)
+    assert np.allclose(fe, M * c[None] * te, rtol=0, atol=1e-12)
+    assert np.allclose(fh, -DT * th, rtol=0, atol=1e-12)
+
+
+def test_gradient_in_scaled_variables_equals_the_reverse_sweep():
+    # the GPU's form: E~ = M c lambda_E stepped by the forward map, the
+    # objective's source added as M c dg/dE, dL/deps = -(1/dt) sum E~ . dE
+    shape = (10, 9, 11)
+    eps = wl.random_eps(shape, 6, lo=2.1, hi=12.1)
+    steps = 30
+    src = [(2, 5, 4, 3, wl.sine_source(steps, DT, 9.0))]
+    mode = np.asarray(wl.uniform_pm1(7, 9 * 11)).reshape(9, 11)
+    obj = adj.Objective(k0=6, mode=mode, window=11)
+    f0 = np.zeros((6,) + shape)
+    L, g = adj.gradient(shape, eps, f0, steps, src, obj, DT)
+    _, hist, c = adj.forward(shape, eps, f0, steps, src, obj, DT)
+    M = adj.pec_mask(shape)
+
+    def source_of(n):
+        s = np.zeros((3,) + shape)
+        if obj.weight(n, steps):
+            s[2, obj.k0] = 2.0 * obj.overlap(hist[n]) * obj.mode
+        return M * c[None] * s
+
+    et, ht = source_of(steps), np.zeros((3,) + shape)
+    g2 = np.zeros(shape)
+    for n in range(steps - 1, -1, -1):
+        g2 -= (et * (hist[n + 1] - hist[n])).sum(0) / DT
+        et, ht = adj.yee_step(et, ht, c, DT, M)
+        et = et + source_of(n)
+    assert np.abs(g2 - g).max() <= 1e-12 * np.abs(g).max()
