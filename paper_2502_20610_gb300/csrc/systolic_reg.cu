@@ -98,7 +98,15 @@ struct RegTile {
     static_assert(NR <= 16 && TY <= 16, "cooperative entries: row < 16, warp offset < 16");
     static_assert(NZ % 4 == 0, "rows move in groups of four (16-byte accesses) and pairs (packed rounding)");
     // shared memory, in floats
-    static constexpr int XE_F = RY * NZ * 32;    // one exchanged component
+    // y-neighbour exchange, one component.  VX (16-bit storage): [warp][lane]
+    // [row], rows moved in 16-byte groups of four; a lane's rows start XR
+    // floats after the previous lane's, XR / 4 odd, so the 8 lanes of a
+    // quarter warp hit disjoint banks.  FP32: [warp][row][lane], one row per
+    // access (measured faster there: 176 vs 169 GCUPS at 256^3, while 16-bit
+    // storage gains 156 -> 164 from the vector form)
+    static constexpr bool VX = S_::narrow;
+    static constexpr int XR = (NZ_ / 4) % 2 ? NZ_ : NZ_ + 4;
+    static constexpr int XE_F = VX ? RY * 32 * XR : RY * NZ_ * 32;
     // lower-shell staging, filled per step by bulk tensor copies (TMA) of
     // boxes whose x start is rounded down to 16 bytes (XA elements): SW =
     // 32 + XA elements cover the 32-wide x window.  One copy per shell
@@ -342,10 +350,16 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
     // of dt/eps (and ca); the pointers below are buffer 0's, buffer b is
     // R::STG_B bytes further
     char *const stg0 = reinterpret_cast<char *>(smem4);
-    float *const XEx = reinterpret_cast<float *>(stg0 + R::NBUF * R::STG_B);  // [warp][row i = 0..NZ-1][lane]: E^t (level t-1) rows r = i-1
+    // y exchange (layout: RegTile::VX): E^t (level t-1) rows i = 0..NZ-1, and
+    // the new H rows r = 1..NZ at row r-1
+    float *const XEx = reinterpret_cast<float *>(stg0 + R::NBUF * R::STG_B);
     float *const XEz = XEx + R::XE_F;
-    float *const XHx = XEz + R::XE_F;      // [warp][row i-1][lane]: new H rows r = 0..NZ-1
+    float *const XHx = XEz + R::XE_F;
     float *const XHz = XHx + R::XE_F;
+    // element (warp, row, lane) of one exchanged component
+    auto xe_at = [](int wq, int row, int ln) {
+        return R::VX ? (wq * 32 + ln) * R::XR + row : (wq * NZ + row) * 32 + ln;
+    };
     // dt/eps of each column, indexed by physical z mod CR: a cell's coefficient
     // stays in place while the skewed register rows move past it
     float *const CEs = XHz + R::XE_F;      // [warp][physical z mod CR][lane]
@@ -629,10 +643,19 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             const int xw = (bx - 1) + ((lane - bx + 1) & 31);
 
             // A. publish E^t (old) rows for the warp below's H half-step
+            if constexpr (R::VX) {
+                float *const qx = XEx + xe_at(w, 0, lane), *const qz = XEz + xe_at(w, 0, lane);
 #pragma unroll
-            for (int i = 0; i < NZ; ++i) {
-                XEx[(w * NZ + i) * 32 + lane] = ex[i];
-                XEz[(w * NZ + i) * 32 + lane] = ez[i];
+                for (int i = 0; i < NZ; i += 4) {
+                    *reinterpret_cast<float4 *>(qx + i) = make_float4(ex[i], ex[i + 1], ex[i + 2], ex[i + 3]);
+                    *reinterpret_cast<float4 *>(qz + i) = make_float4(ez[i], ez[i + 1], ez[i + 2], ez[i + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NZ; ++i) {
+                    XEx[xe_at(w, i, lane)] = ex[i];
+                    XEz[xe_at(w, i, lane)] = ez[i];
+                }
             }
             __syncthreads();  // B1
             if (s_abort) { abort = true; break; }
@@ -686,17 +709,26 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 // rows in pairs (i, i-1), both computed from the old values
                 // before either is written, so 16-bit storage rounds two new
                 // values with one packed conversion
+                const float *const qx = XEx + xe_at(wn, 0, lane), *const qz = XEz + xe_at(wn, 0, lane);
                 auto h_pass = [&](auto masked) {
+                    float4 gx, gz;  // VX: the y+1 neighbour's E rows 4q .. 4q+3
 #pragma unroll
                     for (int i = NR - 1; i >= 2; i -= 2) {
+                        if (R::VX && i % 4 == 0) {  // rows i-4 .. i-1
+                            gx = *reinterpret_cast<const float4 *>(qx + i - 4);
+                            gz = *reinterpret_cast<const float4 *>(qz + i - 4);
+                        }
                         float nh[2][3];
 #pragma unroll
                         for (int k = 0; k < 2; ++k) {
                             const int r = i - k;
                             const float ez_xp = shfl_from(ez[r - 1], src);
                             const float ey_xp = shfl_from(ey[r - 1], src);
-                            const float ez_yp = XEz[(wn * NZ + (r - 1)) * 32 + lane];
-                            const float ex_yp = XEx[(wn * NZ + (r - 1)) * 32 + lane];
+                            const int m = (r - 1) & 3;
+                            const float ez_yp = !R::VX ? qz[(r - 1) * 32]
+                                                : m == 0 ? gz.x : m == 1 ? gz.y : m == 2 ? gz.z : gz.w;
+                            const float ex_yp = !R::VX ? qx[(r - 1) * 32]
+                                                : m == 0 ? gx.x : m == 1 ? gx.y : m == 2 ? gx.z : gx.w;
                             nh[k][0] = h_x(hx[r - 1], ez_yp, ez[r - 1], ey[r], ey[r - 1], ndt);
                             nh[k][1] = h_y(hy[r - 1], ex[r], ex[r - 1], ez_xp, ez[r - 1], ndt);
                             nh[k][2] = h_z(hz[r - 1], ey_xp, ey[r - 1], ex_yp, ex[r - 1], ndt);
@@ -797,10 +829,19 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                     }
                 }
             }
+            if constexpr (R::VX) {
+                float *const qx = XHx + xe_at(w, 0, lane), *const qz = XHz + xe_at(w, 0, lane);
 #pragma unroll
-            for (int i = 1; i < NR; ++i) {
-                XHx[(w * NZ + (i - 1)) * 32 + lane] = hx[i];
-                XHz[(w * NZ + (i - 1)) * 32 + lane] = hz[i];
+                for (int i = 1; i < NR; i += 4) {
+                    *reinterpret_cast<float4 *>(qx + i - 1) = make_float4(hx[i], hx[i + 1], hx[i + 2], hx[i + 3]);
+                    *reinterpret_cast<float4 *>(qz + i - 1) = make_float4(hz[i], hz[i + 1], hz[i + 2], hz[i + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 1; i < NR; ++i) {
+                    XHx[xe_at(w, i - 1, lane)] = hx[i];
+                    XHz[xe_at(w, i - 1, lane)] = hz[i];
+                }
             }
             __syncthreads();  // B2
             if (s_abort) { abort = true; break; }
@@ -837,17 +878,26 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
                 const int wm = (w - 1) & (R::RY - 1);
                 const int src = (lane - 1) & 31;
                 const bool ux = py > 0, uy = px > 0, uz = px > 0 && py > 0;
+                const float *const qx = XHx + xe_at(wm, 0, lane), *const qz = XHz + xe_at(wm, 0, lane);
                 auto e_pass = [&](auto round, auto masked) {
+                    float4 gx, gz;  // VX: the y-1 neighbour's new H rows 4q .. 4q+3
 #pragma unroll
                     for (int i = NR - 1; i >= 2; i -= 2) {
+                        if (R::VX && i % 4 == 0) {  // rows i-4 .. i-1
+                            gx = *reinterpret_cast<const float4 *>(qx + i - 4);
+                            gz = *reinterpret_cast<const float4 *>(qz + i - 4);
+                        }
                         float ne[2][3];
 #pragma unroll
                         for (int k = 0; k < 2; ++k) {
                             const int r = i - k;
                             const float hz_xm = shfl_from(hz[r], src);
                             const float hy_xm = shfl_from(hy[r], src);
-                            const float hx_ym = XHx[(wm * NZ + (r - 1)) * 32 + lane];
-                            const float hz_ym = XHz[(wm * NZ + (r - 1)) * 32 + lane];
+                            const int m = (r - 1) & 3;
+                            const float hx_ym = !R::VX ? qx[(r - 1) * 32]
+                                                : m == 0 ? gx.x : m == 1 ? gx.y : m == 2 ? gx.z : gx.w;
+                            const float hz_ym = !R::VX ? qz[(r - 1) * 32]
+                                                : m == 0 ? gz.x : m == 1 ? gz.y : m == 2 ? gz.z : gz.w;
                             const float c = CEs[(w * CR + ((bz + r - 1) & (CR - 1))) * 32 + lane];
                             const float a = R::LOSSY ? CAs[(w * CR + ((bz + r - 1) & (CR - 1))) * 32 + lane] : 1.f;
                             ne[k][0] = e_x(decay<R::LOSSY>(a, ex[r - 1]), hz[r], hz_ym, hy[r], hy[r - 1], c);
