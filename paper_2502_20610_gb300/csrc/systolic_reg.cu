@@ -631,10 +631,13 @@ __global__ void __launch_bounds__(R::NT, 1) systolic_reg_kernel(const __grid_con
             const long long col = px + (long long)P.pitch * py;
             // rows i with physical z = bz + i - 1 inside the domain
             const int i_lo = max(1, 1 - bz), i_hi = min(NR, P.nz - bz + 1);
-            // the box lies inside the domain, clear of the low walls: every
-            // box cell is updated with no mask.  (The x-shell lane and the
-            // y-shell warp compute values that their refills overwrite.)
-            const bool inner = bx >= 1 && by >= 1 && bz >= 1 && bx + TX <= P.nx && by + TY <= P.ny && bz + TZ <= P.nz;
+            // the box is clear of the low walls: every box cell is updated
+            // with no mask.  (The x-shell lane and the y-shell warp compute
+            // values that their refills overwrite.)  Cells beyond the high
+            // walls need none either: their dt/eps (and c_a) is 0 (the
+            // coefficient shells are zero-filled off the domain), so their E
+            // stays 0, and their H, whose curl reads only such E, stays 0 too.
+            const bool inner = bx >= 1 && by >= 1 && bz >= 1;
             // every row of the box's z range lies in the domain (rows refilled
             // from the face buffers need no clearing)
             const bool zin = bz >= 0 && bz + TZ <= P.nz;
