@@ -240,10 +240,10 @@ fdtd_status fdtd_debug_set(fdtd_handle h, int32_t kind, int64_t ticket, int64_t 
  * tile schedule does not fit it even one step per launch are rejected with
  * FDTD_ERR_UNSUPPORTED (the message names the sizes); cubic grids up to
  * about 1900^3 cells fit.
- * The first call on a device looks up the array's device address and sets the
- * kernel's shared-memory limit; make that first call before any stream
- * capture.  Every call shares the array and clears it first, so calls that
- * overlap on the GPU (two streams, two threads) race: serialise them.
+ * The first call on a device looks up the array's device address and sets
+ * the kernel's shared-memory limit.  Every call shares the array and clears
+ * it first, so calls that overlap on the GPU (two streams, two threads)
+ * race: serialise them.
  * The call is synchronous: it returns after the steps finish, with
  * FDTD_ERR_TIMEOUT if a device wait ran out, FDTD_ERR_CUDA on a CUDA error,
  * FDTD_ERR_INVALID_ARG for null pointers, an extent above 2^20, n_steps < 0
