@@ -733,15 +733,27 @@ def main():
         sim.step(STEPS_PER_CALL)
         sim.read_fields(out=host_out)
         barrier(world)
+        # device time of the steps inside the loop (CUDA events around each
+        # call's launches) and clocks, so the line shows what the copies add
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        eclk = ClockSampler(local)
+        eclk.start()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for q in range(args.steps):
             sim.write_fields_ptr(host_in.data_ptr())
+            ev[q][0].record(stream)
             sim.step(STEPS_PER_CALL)
+            ev[q][1].record(stream)
             sim.read_fields_ptr(0x3F, host_out.data_ptr())
         te = time.perf_counter() - t0
+        e_clk = eclk.stop()
+        dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
         te = max_over_ranks(te, world, device)
         e2e = {"value": world * cells * STEPS_PER_CALL * args.steps / te / 1e9, "unit": "GCUPS",
-               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
+               "ms_per_step": 1e3 * te / args.steps, "device_ms_per_step": 1e3 * dev_s / args.steps,
+               "clocks": e_clk}
     sim.close()
 
     # the same workload with 16-bit field storage (FP32 arithmetic), both schedules
