@@ -118,10 +118,11 @@ bool make_layout(const fdtd_grid &g, const fdtd_coeffs &c, const fdtd_boundary &
         L.nband = cells_within(g, 2);   // their stencils reach one cell further
         L.params = off;
         off = align_up(off + sizeof(float) * (size_t)mlpnet::NPARAM);
+        // two band snapshots (S^{n-1}, S^n), each six components and its x slab
         L.prev = off;
-        off = align_up(off + 6 * align_up(sizeof(float) * (size_t)n));
+        off = align_up(off + 6 * align_up(sizeof(float) * (size_t)n) + learned_xslab_bytes(g.ny, g.nz));
         L.snap = off;
-        off = align_up(off + 6 * align_up(sizeof(float) * (size_t)n));
+        off = align_up(off + 6 * align_up(sizeof(float) * (size_t)n) + learned_xslab_bytes(g.ny, g.nz));
         L.layer = off;
         off = align_up(off + 3 * sizeof(int) * (size_t)L.nlayer);
         L.band = off;
@@ -781,12 +782,13 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
             const long long fs = (long long)(h->L.fields[1] - h->L.fields[0]) / 4;
             const long long ps = (long long)align_up(sizeof(float) * (size_t)h->L.pitch * h->g.ny * h->g.nz) / 4;
             if (fs != ps) return FDTD_ERR_STATE;  // previous-state arrays mirror the field layout
-            // per step: snapshot the band of S^n; the network (S^n and S^{n-1}
+            // per step: snapshot the band of S^n (and its x slab); the network (S^n and S^{n-1}
             // bands -> corrections) on the internal stream, the Yee step on the
             // caller's, both at once; then the corrections are added and the
             // snapshot becomes the next step's previous state
             for (int64_t s = 0; s < n; ++s) {
                 CK(learned_copy_cells(h->snap, f0, fs, h->L.pitch, h->g.ny, h->band, (int)h->L.nband, h->stream));
+                CK(learned_fill_xslab(h->snap, f0, fs, h->L.pitch, h->g.nx, h->g.ny, h->g.nz, h->stream));
                 CK(cudaEventRecord(h->ev_fork, h->stream));
                 CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
                 CK(learned_layer_predict(h->params, h->snap, h->prev, fs, h->L.pitch, h->g.nx, h->g.ny, h->g.nz,
@@ -798,7 +800,7 @@ fdtd_status fdtd_step(fdtd_handle h, int64_t n)
                 CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
                 CK(learned_layer_scatter(f0, fs, h->L.pitch, h->g.ny, h->layer, (int)h->L.nlayer, h->pred, h->stream));
                 std::swap(h->prev, h->snap);
-                h->launches += 5;
+                h->launches += 6;
                 h->step += 1;
             }
             return FDTD_OK;

@@ -454,6 +454,74 @@ constexpr int SM_W1T = NIP * NH, SM_W2T = NH * NH, SM_W3T = NH * NO, SM_XT = NIP
 constexpr size_t LAYER_SMEM =
     sizeof(float) * (SM_W1T + SM_W2T + SM_XT + 2 * SM_H + SM_W3T + 2 * NH + NO + 2 * LC + 4 * LC);
 
+// Asynchronous 4-byte copy, global -> shared (cp.async, cached in L1).  With
+// valid == false nothing is read and the shared word is zero-filled; src is
+// then still an address inside the field array.
+__device__ __forceinline__ void cp_async_4(float *dst, const float *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Each band snapshot (six components at c * fstride, rows of `pitch`) is
+// followed by its x slab: the planes x = 0, 1 (side 0) and x = nx-2, nx-1
+// (side 1) of every component, y fastest, [comp][side][xd][z][y], so that
+// the stencils of the cells on the two x faces (a full row apart from each
+// other in the snapshot) are read with consecutive y across the lanes.
+__device__ __host__ __forceinline__ long long xslab_floats(int ny, int nz) { return 24LL * ny * nz; }
+
+// Stage the unnormalised stencils of `tile` into Xt ([k][cell], swizzled)
+// with asynchronous copies: thread -> cell q = tid % 64 and three of the
+// twelve (level, component) pairs, (tid / 64) * 3 + 0..2, each a 27-cell
+// stencil; neighbour offsets are unrolled, validity is per axis, neighbours
+// outside the domain and cells past the list are zero.  Cells on an x face
+// read the x slab, the others the snapshot itself (same values).
+__device__ __forceinline__ void stage_stencils(float *Xt, const float *__restrict__ cur,
+                                               const float *__restrict__ prev, long long fstride, int pitch,
+                                               int nx, int ny, int nz, const int *__restrict__ cells, int ncells,
+                                               int tile)
+{
+    const int tid = threadIdx.x, q = tid & (LC - 1), p0 = (tid >> 6) * 3;
+    const int cell = tile * LC + q;
+    if (cell < ncells) {
+        const int x = cells[3 * cell], y = cells[3 * cell + 1], z = cells[3 * cell + 2];
+        const bool vx[3] = {x > 0, true, x + 1 < nx}, vy[3] = {y > 0, true, y + 1 < ny},
+                   vz[3] = {z > 0, true, z + 1 < nz};
+        const long long nyz = (long long)ny * nz;
+        // address of (x', y', z') of component c: level base + c * cs + o0 + x' sx + y' sy + z' sz
+        long long sx = 1, sy = pitch, sz = (long long)pitch * ny, cs = fstride, o0 = 0;
+        if (x == 0 || x == nx - 1) {
+            const int side = x == 0 ? 0 : 1, base = side ? nx - 2 : 0;
+            sx = nyz, sy = 1, sz = ny, cs = 4 * nyz;
+            o0 = 6 * fstride + (2 * side - base) * nyz;
+        }
+        const long long centre = o0 + x * sx + y * sy + z * sz;
+        const long long ox[3] = {-sx, 0, sx}, oy[3] = {-sy, 0, sy}, oz[3] = {-sz, 0, sz};
+#pragma unroll 1
+        for (int pq = 0; pq < 3; ++pq) {
+            const int pr = p0 + pq, lev = pr / 6, comp = pr - lev * 6;
+            const float *src = (lev == 0 ? cur : prev) + comp * cs + centre;
+#pragma unroll
+            for (int d = 0; d < 27; ++d) {
+                const int dx = d % 3, dy = (d / 3) % 3, dz = d / 9;
+                const int k = pr * 27 + d;
+                const bool ok = vx[dx] && vy[dy] && vz[dz];
+                const float *a = ok ? src + (ox[dx] + oy[dy] + oz[dz]) : src;
+                cp_async_4(&Xt[k * LC + swz(k, q)], a, ok);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq)
+#pragma unroll
+            for (int d = 0; d < 27; ++d) {
+                const int k = (p0 + pq) * 27 + d;
+                Xt[k * LC + swz(k, q)] = 0.f;
+            }
+    }
+}
+
 __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__ P, const float *__restrict__ cur,
                                                        const float *__restrict__ prev, long long fstride, int pitch,
                                                        int nx, int ny, int nz, const int *__restrict__ cells,
@@ -471,6 +539,10 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
     float *ir = rr + LC;              // 1/r per cell (0 if r = 0)
     float *part = ir + LC;            // [4][cell] partial sums of x^2
     const int tid = threadIdx.x;
+    const int ntiles = (ncells + LC - 1) / LC;
+    // the first tile's stencils are in flight while the weights are loaded
+    if ((int)blockIdx.x < ntiles)
+        stage_stencils(Xt, cur, prev, fstride, pitch, nx, ny, nz, cells, ncells, blockIdx.x);
     for (int e = tid; e < NH * NI; e += 256) {
         const int u = e / NI, k = e - u * NI;
         W1t[k * NH + swz(k, u)] = P[OFF_W1 + e];
@@ -489,46 +561,22 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
         b2[tid] = P[OFF_B2 + tid];
     }
     if (tid < NO) b3[tid] = P[OFF_B3 + tid];
-    const long long sxy = (long long)pitch * ny;
-    const int ntiles = (ncells + LC - 1) / LC;
+    Xt[NI * LC + tid] = 0.f;  // padding rows of the stencil (256 zeros), never staged over
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        __syncthreads();  // previous tile done with Xt / H / rr
-        // gather: thread -> cell q = tid % 64 and three of the twelve (level,
-        // component) pairs, (tid / 64) * 3 + 0..2, each a 27-cell stencil;
-        // neighbour offsets are unrolled, validity is per axis
+        cp_async_wait_all();
+        __syncthreads();  // this tile's stencils have landed; the previous tile is done with H / rr
         {
+            // sum of squares of the thread's own 81 staged values, in staging order
             const int q = tid & (LC - 1), p0 = (tid >> 6) * 3;
-            const int cell = tile * LC + q;
             float ss = 0.f;
-            if (cell < ncells) {
-                const int x = cells[3 * cell], y = cells[3 * cell + 1], z = cells[3 * cell + 2];
-                const bool vx[3] = {x > 0, true, x + 1 < nx}, vy[3] = {y > 0, true, y + 1 < ny},
-                           vz[3] = {z > 0, true, z + 1 < nz};
-                const long long centre = x + (long long)pitch * y + sxy * z;
 #pragma unroll
-                for (int pq = 0; pq < 3; ++pq) {
-                    const int pr = p0 + pq, lev = pr / 6, comp = pr - lev * 6;
-                    const float *src = (lev == 0 ? cur : prev) + comp * fstride + centre;
+            for (int pq = 0; pq < 3; ++pq)
 #pragma unroll
-                    for (int d = 0; d < 27; ++d) {
-                        const int dx = d % 3, dy = (d / 3) % 3, dz = d / 9;
-                        const int k = pr * 27 + d;
-                        float v = 0.f;
-                        if (vx[dx] && vy[dy] && vz[dz]) v = src[(dx - 1) + (long long)pitch * (dy - 1) + sxy * (dz - 1)];
-                        Xt[k * LC + swz(k, q)] = v;
-                        ss = __fmaf_rn(v, v, ss);
-                    }
+                for (int d = 0; d < 27; ++d) {
+                    const int k = (p0 + pq) * 27 + d;
+                    const float v = Xt[k * LC + swz(k, q)];
+                    ss = __fmaf_rn(v, v, ss);
                 }
-            } else {
-#pragma unroll
-                for (int pq = 0; pq < 3; ++pq)
-#pragma unroll
-                    for (int d = 0; d < 27; ++d) {
-                        const int k = (p0 + pq) * 27 + d;
-                        Xt[k * LC + swz(k, q)] = 0.f;
-                    }
-            }
-            Xt[NI * LC + tid] = 0.f;  // padding rows of the stencil (256 zeros)
             part[(tid >> 6) * LC + q] = ss;
         }
         __syncthreads();
@@ -555,7 +603,10 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
                     const int cell = m0 + g + 8 * (e >> 1), unit = n0 + 8 * j + 2 * q + (e & 1);
                     H1t[unit * LC + swz(unit, cell)] = tanhf(__fmaf_rn(acc[j][e], ir[cell], b1[unit]));
                 }
-            __syncthreads();
+            __syncthreads();  // every warp is past layer 1's reads of Xt
+            // the next tile's stencils fly while layers 2 and 3 run
+            const int next = tile + gridDim.x;
+            if (next < ntiles) stage_stencils(Xt, cur, prev, fstride, pitch, nx, ny, nz, cells, ncells, next);
             warp_gemm_3xtf32<NH>(H1t, W2t, acc);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -577,6 +628,7 @@ __global__ void __launch_bounds__(256, 1) layer_kernel(const float *__restrict__
             out[(long long)cell * NO + o] = (m >> o) & 1u ? __fmul_rn(rr[q], f) : 0.f;
         }
     }
+    cp_async_wait_all();  // nothing left in flight at exit
 }
 
 __global__ void __launch_bounds__(256) scatter_kernel(float *__restrict__ f, long long fstride, int pitch, int ny,
@@ -597,6 +649,25 @@ __global__ void __launch_bounds__(256) copy_cells_kernel(float *__restrict__ dst
     if (q >= ncells) return;
     const long long p = cells[3 * q] + (long long)pitch * (cells[3 * q + 1] + (long long)ny * cells[3 * q + 2]);
     for (int c = 0; c < NO; ++c) dst[c * fstride + p] = src[c * fstride + p];
+}
+
+// The x slab of a band snapshot (layout above): element e of the slab is
+// (comp, side, xd, z, y) in that order, y fastest; planes outside the grid
+// (nx < 2) are zero and never read.
+__global__ void __launch_bounds__(256) fill_xslab_kernel(float *__restrict__ snap, const float *__restrict__ f,
+                                                         long long fstride, int pitch, int nx, int ny, int nz)
+{
+    const long long n = xslab_floats(ny, nz);
+    float *slab = snap + 6 * fstride;
+    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
+        const int y = (int)(e % ny);
+        long long r = e / ny;
+        const int z = (int)(r % nz);
+        r /= nz;
+        const int xd = (int)(r & 1), side = (int)((r >> 1) & 1), comp = (int)(r >> 2);
+        const int x = side ? nx - 2 + xd : xd;
+        slab[e] = (x >= 0 && x < nx) ? f[comp * fstride + x + (long long)pitch * (y + (long long)ny * z)] : 0.f;
+    }
 }
 
 } // namespace
@@ -704,5 +775,16 @@ cudaError_t learned_copy_cells(float *dst, const float *src, long long fstride, 
 {
     if (ncells <= 0) return cudaSuccess;
     copy_cells_kernel<<<(ncells + 255) / 256, 256, 0, st>>>(dst, src, fstride, pitch, ny, cells, ncells);
+    return cudaGetLastError();
+}
+
+size_t learned_xslab_bytes(int ny, int nz) { return sizeof(float) * (size_t)xslab_floats(ny, nz); }
+
+cudaError_t learned_fill_xslab(float *snap, const float *f, long long fstride, int pitch, int nx, int ny, int nz,
+                               cudaStream_t st)
+{
+    const long long n = xslab_floats(ny, nz);
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+    fill_xslab_kernel<<<blocks, 256, 0, st>>>(snap, f, fstride, pitch, nx, ny, nz);
     return cudaGetLastError();
 }

@@ -29,8 +29,9 @@ cudaError_t mlp_record(const float *prev, const float *cur, const float *nxt, lo
 
 // Layer update of a simulation step (FP32 fields at f + c*fstride, rows of
 // `pitch`): corrections r f for `ncells` layer cells (x,y,z triplets) from
-// the current and previous states into out [ncells][6]; scatter adds them
-// to the cells after the Yee step.
+// the current and previous band snapshots (each followed by its x slab,
+// below) into out [ncells][6]; scatter adds them to the cells after the Yee
+// step.
 size_t learned_layer_smem();
 cudaError_t learned_layer_configure();
 cudaError_t learned_layer_predict(const float *params, const float *cur, const float *prev, long long fstride,
@@ -40,3 +41,10 @@ cudaError_t learned_layer_scatter(float *f, long long fstride, int pitch, int ny
                                   const float *vals, cudaStream_t st);
 cudaError_t learned_copy_cells(float *dst, const float *src, long long fstride, int pitch, int ny, const int *cells,
                                int ncells, cudaStream_t st);
+// A band snapshot (6 * fstride floats) is followed by its x slab: the planes
+// x = 0, 1, nx-2, nx-1 of the six components, y fastest, which the layer
+// update reads for the cells on the two x faces.  learned_fill_xslab copies
+// them from the fields f into the slab of `snap`.
+size_t learned_xslab_bytes(int ny, int nz);
+cudaError_t learned_fill_xslab(float *snap, const float *f, long long fstride, int pitch, int nx, int ny, int nz,
+                               cudaStream_t st);
