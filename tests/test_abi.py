@@ -110,7 +110,12 @@ def test_boundary_option_checks(lib):
     model = np.zeros(fdtd.mlp_param_count(), np.float32)
     st, n_l = _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive", boundary="learned",
                                          learned=(4, model)))
-    assert st == 0 and n_l > _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive"))[1]
+    n_plain = _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, scheme="naive"))[1]
+    assert st == 0 and n_l > n_plain
+    # two band snapshots (S^n, S^{n-1}), each six FP32 components and its x
+    # slab (the planes x = 0, 1, nx-2, nx-1 of the six components)
+    nz, ny, nx = shape
+    assert n_l - n_plain >= 2 * (6 * 4 * nx * ny * nz + 4 * 24 * ny * nz)
     # the layer update needs the previous level every step: naive scheme, FP32
     assert _ws(lib, *fdtd.make_params(shape, wl.DT_DEFAULT, boundary="learned",
                                       learned=(4, model)))[0] == fdtd.FDTD_ERR_UNSUPPORTED
