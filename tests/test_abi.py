@@ -142,6 +142,19 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.fdtd_status_string(99) == b"unknown status"
 
 
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the binding raises (there is no CPU path to
+    fall back to).  A fresh interpreter, since the loaded library is cached."""
+    import subprocess
+    import sys
+    missing = str(tmp_path / "libfdtd.so")
+    code = ("import sys; sys.path.insert(0, %r); from paper_2502_20610_gb300 import fdtd; "
+            "fdtd.load_library(%r)" % (ROOT, missing))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0
+    assert "is not built" in r.stderr and "no CPU fallback" in r.stderr
+
+
 def test_product_path_has_no_oracle_import():
     """The library binding never reaches the oracle (no CPU fallback)."""
     pkg = os.path.join(ROOT, "paper_2502_20610_gb300")
